@@ -1,0 +1,252 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module holds problem set-ups only -- grid sizes, rates, boundary kinds,
+boundary states and initial macroscopic fields -- and none of the scheme's
+arithmetic. Both sides (the CUDA library through its binding, and the CPU
+oracle) receive exactly these arrays.
+
+A ``Workload`` describes one 2D problem:
+  nx, ny      interior nodes (x fastest in every array, shape (ny, nx))
+  dx, dy, dt  grid spacing and time step
+  s           the 16 diagonal relaxation rates s_1..s_16 (s_1..s_4 unused)
+  bc          four (kind, state) pairs for the sides x-, x+, y-, y+;
+              kind in {"periodic", "eq", "reflect", "extrap", "wall"};
+              state = (rho, u, v, T) for "eq" and "wall" (the wall takes rho
+              from the adjacent node), else None
+  rho,u,v,T   initial fields, float64 arrays of shape (ny, nx)
+  nsteps      the number of steps of the full run
+
+Boundary states that are post-shock states were computed with the
+Rankine-Hugoniot relations at gamma = 2 (``tests/golden/make_states.py``,
+which calls only the oracle); a test checks them.
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+BC_KINDS = ("periodic", "eq", "reflect", "extrap", "wall")
+
+
+def rates(default=1e5, **given):
+    """16 relaxation rates: ``default`` everywhere, s_k overridden by the
+    keyword s<k> (1-based, as in the paper)."""
+    s = [float(default)] * 16
+    for key, val in given.items():
+        k = int(key[1:])
+        s[k - 1] = float(val)
+    return tuple(s)
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    dx: float
+    dy: float
+    dt: float
+    s: tuple
+    bc: tuple
+    rho: np.ndarray
+    u: np.ndarray
+    v: np.ndarray
+    T: np.ndarray
+    nsteps: int = 1
+    meta: dict = field(default_factory=dict)
+
+    def cfg(self):
+        """Plain dict of the scheme parameters (the oracle's input)."""
+        return {"nx": self.nx, "ny": self.ny, "dx": self.dx, "dy": self.dy,
+                "dt": self.dt, "s": self.s, "bc": self.bc}
+
+    def fields(self):
+        return self.rho, self.u, self.v, self.T
+
+
+def _fill(nx, ny, state):
+    return [np.full((ny, nx), float(x)) for x in state]
+
+
+# ----------------------------------------------------------------------------
+# Shock tubes (Sec. V.A)
+# ----------------------------------------------------------------------------
+SOD_L = (1.0, 0.0, 0.0, 1.0)
+SOD_R = (0.125, 0.0, 0.0, 0.8)
+LAX_L = (0.445, 0.698, 0.0, 7.928)
+LAX_R = (0.5, 0.0, 0.0, 1.142)
+
+# Sod rates of Sec. V.A(a) and the same rates scaled by the grid ratio
+# 0.005/0.002 -> x0.4 for the coarser 200-node tube (stable variant).
+SOD_RATES_PAPER = rates(s5=500, s6=500, s7=1e3, s8=1e3, s11=2500)
+SOD_RATES_STABLE = rates(s5=200, s6=200, s7=400, s8=400, s11=1000)
+SOD_RATES_LITERAL = rates()
+
+
+def shock_tube(left, right, nx, dx, dt, nsteps, s, ny=1, x_interface=None,
+               name="shock_tube"):
+    """Quasi-1D tube: nx x ny nodes, y periodic, x sides held at the initial
+    left/right equilibria (Sec. V.A). Node i sits at x = (i + 1/2) dx; nodes
+    with x <= x_interface take the left state (default: the middle)."""
+    if x_interface is None:
+        x_interface = 0.5 * nx * dx
+    x = (np.arange(nx) + 0.5) * dx
+    left_mask = np.broadcast_to(x <= x_interface, (ny, nx))
+    f = [np.where(left_mask, a, b) for a, b in zip(left, right)]
+    bc = (("eq", tuple(left)), ("eq", tuple(right)),
+          ("periodic", None), ("periodic", None))
+    return Workload(name, nx, ny, dx, dx, dt, tuple(s), bc, *f, nsteps=nsteps,
+                    meta={"x_interface": x_interface, "left": left, "right": right})
+
+
+def sod_config1(rates_kind="literal", ny=4):
+    """Sod tube on 200 x ny nodes, dx = dy = 0.005, dt = 1e-5, 10 000 steps
+    (t = 0.1), interface at x = 0.5. ``rates_kind``: "literal" (all s = 1e5),
+    "stable" (the paper's Sod rates x 0.4) or "paper"."""
+    s = {"literal": SOD_RATES_LITERAL, "stable": SOD_RATES_STABLE,
+         "paper": SOD_RATES_PAPER}[rates_kind]
+    return shock_tube(SOD_L, SOD_R, 200, 0.005, 1e-5, 10000, s, ny=ny,
+                      name="sod_200x%d_%s" % (ny, rates_kind))
+
+
+def sod_paper_case1():
+    """Sec. V.A(a) case 1: dx = 0.002, dt = 2e-6, t = 0.18 on x in [-0.5, 0.5]
+    (500 nodes; the domain length is not stated in the paper)."""
+    return shock_tube(SOD_L, SOD_R, 500, 0.002, 2e-6, 90000, SOD_RATES_PAPER,
+                      name="sod_paper_case1")
+
+
+# ----------------------------------------------------------------------------
+# Regular shock reflection (Sec. V.B.a geometry)
+# ----------------------------------------------------------------------------
+# Paper's Mach-5 problem: inflow (1, 5, 0, 0.5), top (2.27273, 4.3, -1.21244, 1.76).
+REFLECT_M5_IN = (1.0, 5.0, 0.0, 0.5)
+REFLECT_M5_TOP = (2.27273, 4.3, -1.21244, 1.76)
+# Mach 2.9 inflow with pre-shock rho = 1, T = 1 (sound speed sqrt(2) at
+# gamma = 2), 30-degree incident shock: post-shock state from the oblique
+# Rankine-Hugoniot relations (T = p / rho).
+REFLECT_M29_IN = (1.0, 2.9 * math.sqrt(2.0), 0.0, 1.0)
+REFLECT_M29_TOP = (1.5374771480804381, 3.742789341797761, -0.6208189520502188,
+                   1.6065279429250885)
+REFLECT_RATES = rates(s5=1e4, s6=2e3, s7=1e4, s8=1e4)
+
+
+def regular_reflection(nx=600, ny=200, dx=1e-3, dt=2e-6, nsteps=20000,
+                       inflow=REFLECT_M29_IN, top=REFLECT_M29_TOP):
+    """Left: inflow held (Dirichlet); top: post-shock state held; bottom:
+    reflecting wall; right: linear extrapolation; interior starts at the
+    inflow state (Sec. V.B.a)."""
+    f = _fill(nx, ny, inflow)
+    bc = (("eq", tuple(inflow)), ("extrap", None), ("reflect", None),
+          ("eq", tuple(top)))
+    return Workload("regular_reflection_%dx%d" % (nx, ny), nx, ny, dx, dx, dt,
+                    REFLECT_RATES, bc, *f, nsteps=nsteps)
+
+
+# ----------------------------------------------------------------------------
+# Shock-bubble interaction (Sec. V.C)
+# ----------------------------------------------------------------------------
+BUBBLE_PRE = (1.0, 0.0, 0.0, 1.0)                 # (rho, u, v, T), p = 1
+BUBBLE_POST = (1.28, -0.3774, 0.0, 1.6512 / 1.28)  # p = 1.6512
+BUBBLE_RATES = rates(s5=1e4, s6=1e4, s7=1e4, s8=1e4)
+
+
+def shock_bubble(nx=2048, ny=1024, dx=1e-3, dt=1e-5, radius=128,
+                 bubble_rho=0.1358, nsteps=2000):
+    """Mach-1.22 planar shock (post-shock gas on the right, moving left) and a
+    light circular bubble in pressure equilibrium (p = 1, T = 1/rho_b), centre
+    (nx/2, ny/2), shock plane ``radius + 32`` nodes to the right of the
+    centre. Right: post-shock inflow held; left: extrapolation; top and
+    bottom: reflecting (Sec. V.C)."""
+    rho, u, v, T = _fill(nx, ny, BUBBLE_PRE)
+    ix = np.arange(nx)[None, :] + 0.5
+    iy = np.arange(ny)[:, None] + 0.5
+    cx, cy = 0.5 * nx, 0.5 * ny
+    inside = (ix - cx) ** 2 + (iy - cy) ** 2 <= radius ** 2
+    rho = np.where(inside, bubble_rho, rho)
+    T = np.where(inside, 1.0 / bubble_rho, T)
+    post = np.broadcast_to(ix > cx + radius + 32, (ny, nx))
+    fields = [np.where(post, p, q) for p, q in zip(BUBBLE_POST, (rho, u, v, T))]
+    bc = (("extrap", None), ("eq", BUBBLE_POST), ("reflect", None),
+          ("reflect", None))
+    return Workload("shock_bubble_%dx%d" % (nx, ny), nx, ny, dx, dx, dt,
+                    BUBBLE_RATES, bc, *fields, nsteps=nsteps)
+
+
+# ----------------------------------------------------------------------------
+# Couette flow (Sec. V.D)
+# ----------------------------------------------------------------------------
+def couette(NX=16, NY=32, d=0.004, dt=1e-5, U=0.1, t_end=57.5, s=None):
+    """Plates at y = -D/2 and +D/2 moving at -U and +U, D = NY d. The walls sit
+    on ghost nodes j = 0 and j = NY, so the evolved rows are j = 1..NY-1 at
+    y_j = -D/2 + j d; x is periodic. Walls hold (u, v, T) = (+-U, 0, 1) and
+    take rho from the adjacent node."""
+    ny = NY - 1
+    rho, u, v, T = _fill(NX, ny, (1.0, 0.0, 0.0, 1.0))
+    bc = (("periodic", None), ("periodic", None),
+          ("wall", (1.0, -U, 0.0, 1.0)), ("wall", (1.0, U, 0.0, 1.0)))
+    nsteps = int(round(t_end / dt))
+    y = -0.5 * NY * d + d * np.arange(1, NY)
+    return Workload("couette_%dx%d" % (NX, NY), NX, ny, d, d, dt,
+                    tuple(s) if s is not None else rates(), bc, rho, u, v, T,
+                    nsteps=nsteps, meta={"U": U, "D": NY * d, "y": y})
+
+
+# ----------------------------------------------------------------------------
+# Seeded random states (parity cases)
+# ----------------------------------------------------------------------------
+def random_state(nx, ny, seed, bc=None, dx=0.01, dt=1e-5, s=None, smooth=True,
+                 umax=0.5, name=None):
+    """Seeded positive states: rho in [0.5, 2], T in [0.5, 1.5],
+    |u|, |v| <= umax. ``smooth`` superposes a few random Fourier modes;
+    otherwise every node is drawn independently."""
+    rng = np.random.default_rng(seed)
+    if s is None:
+        s = tuple(float(x) for x in 10.0 ** rng.uniform(2.0, 5.0, 16))
+    if bc is None:
+        bc = (("periodic", None),) * 4
+    if smooth:
+        X = (np.arange(nx)[None, :] + 0.5) / nx
+        Y = (np.arange(ny)[:, None] + 0.5) / ny
+
+        def field_():
+            out = np.zeros((ny, nx))
+            for _ in range(4):
+                kx, ky = rng.integers(0, 4, 2)
+                ph = rng.uniform(0, 2 * np.pi)
+                out = out + rng.uniform(-1, 1) * np.cos(2 * np.pi * (kx * X + ky * Y) + ph)
+            return out / 4.0
+    else:
+        def field_():
+            return rng.uniform(-1, 1, (ny, nx))
+    rho = 1.25 + 0.75 * field_()
+    u = umax * field_()
+    v = umax * field_()
+    T = 1.0 + 0.5 * field_()
+    return Workload(name or "random_%dx%d_s%d" % (nx, ny, seed), nx, ny, dx, dx,
+                    dt, tuple(s), tuple(bc), rho, u, v, T, nsteps=1)
+
+
+def tube_batch(ntubes=4096, nx_min=128, nx_max=2048, seed=0):
+    """Batched quasi-1D Riemann problems: tube lengths Nx ~ U[nx_min, nx_max]
+    (integers), left/right rho and T log-uniform in [0.1, 10], u uniform in
+    [-1, 1], v = 0. Each tube spans x in [0, 1] (dx = 1/Nx), interface at 0.5,
+    dt = 1e-5, 10 000 steps; the Sod-type rates scale with dx:
+    s5 = s6 = 200 (0.005/dx), s7 = s8 = 400 (0.005/dx), s11 = 1000 (0.005/dx),
+    each capped at 1e5, all others 1e5.
+    Returns a dict of numpy arrays (one row per tube)."""
+    rng = np.random.default_rng(seed)
+    nx = rng.integers(nx_min, nx_max + 1, ntubes)
+    lo, hi = math.log(0.1), math.log(10.0)
+    rho = np.exp(rng.uniform(lo, hi, (ntubes, 2)))
+    T = np.exp(rng.uniform(lo, hi, (ntubes, 2)))
+    u = rng.uniform(-1.0, 1.0, (ntubes, 2))
+    dx = 1.0 / nx
+    scale = 0.005 / dx
+    s = np.full((ntubes, 16), 1e5)
+    for k, base in ((5, 200.0), (6, 200.0), (7, 400.0), (8, 400.0), (11, 1000.0)):
+        s[:, k - 1] = np.minimum(base * scale, 1e5)
+    return {"nx": nx.astype(np.int64), "dx": dx, "dt": 1e-5, "nsteps": 10000,
+            "left": np.stack([rho[:, 0], u[:, 0], np.zeros(ntubes), T[:, 0]], 1),
+            "right": np.stack([rho[:, 1], u[:, 1], np.zeros(ntubes), T[:, 1]], 1),
+            "s": s}
