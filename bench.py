@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Throughput of the fused D2V16 MRT-FD step on GB300.
+
+Workload: the 2D regular shock reflection (Sec. V.B.a geometry) on a 600 x 200
+grid, dx = dy = 1e-3, dt = 2e-6: Mach-2.9 inflow (rho = 1, T = 1) on the left,
+the oblique-shock post-shock state held on the top, a reflecting lower wall
+and linear extrapolation on the right. One benchmark step is one time step of
+the whole hot path (boundary ghosts, moments, equilibria, relaxation,
+back-map, Lax-Wendroff update, watchdog and conservation audit) over the grid.
+
+The grid (15 MB in FP32) fits in the 129 MB L2, so the L2 is flushed (a
+256 MiB write) between timed steps, outside the timed events. Each timed step
+is bracketed by CUDA events on the launching stream; the GPU is kept busy
+while the host enqueues the loop, so host launch latency is not timed.
+
+Lines printed (rank 0): one JSON object. ``value`` is FP32-path cell-updates/s
+summed over ranks; ``fp64`` carries the FP64 path measured the same way;
+``cpu_baseline`` is the FP64 numpy oracle on one host core over a bounded
+sample; ``e2e`` times the same step through the C ABI with host buffers.
+
+``--impl reference`` times the CPU oracle instead (the only reference
+implementation this method has), on the same workload, rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+if "--impl" in sys.argv and "reference" in sys.argv or "--cpu-sample" in sys.argv:
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+
+import numpy as np  # noqa: E402
+
+METRIC = ("D2V16 MRT cell-updates/s at stated error vs FP64 oracle; "
+          "% of HBM roofline")
+UNIT = "cell-updates/s"
+# Algorithmic traffic per cell-update: 16 populations read once and written once.
+BYTES_PER_CELL = {"fp64": 256, "fp32": 128}
+# Algorithmic FP64 operations per cell-update of the factorised step (FMA = 2):
+# transform 28, conserved moments 24, equilibria 40, deviations 77,
+# back-map 64, inverse transform 28, Lax-Wendroff update 128.
+FLOPS_PER_CELL = 389
+FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload():
+    import workloads as W
+    return W.regular_reflection()
+
+
+def config_json(w, precision, audit_every):
+    return {"workload": "regular_shock_reflection_%dx%d" % (w.nx, w.ny),
+            "nx": w.nx, "ny": w.ny, "dx": w.dx, "dt": w.dt, "mach": 2.9,
+            "precision": precision, "audit_every": audit_every,
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing
+# ----------------------------------------------------------------------------
+def oracle_steps(seconds=None, steps=None):
+    """Times oracle steps on the workload; returns (steps, seconds)."""
+    from oracle import scheme
+    w = workload()
+    f = scheme.init_populations(*w.fields())
+    cfg = w.cfg()
+    f = scheme.step(f, cfg)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        f = scheme.step(f, cfg)
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (seconds is not None and el >= seconds):
+            return n, el
+
+
+def cpu_baseline(seconds):
+    """Runs the oracle in a fresh single-threaded process (no GPU state)."""
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(seconds)],
+                         capture_output=True, text=True, timeout=600)
+    if res.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + res.stderr[-200:]}
+    n, el = json.loads(res.stdout.strip().splitlines()[-1])
+    w = workload()
+    return {"value": w.nx * w.ny * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d FP64 numpy oracle steps of the %dx%d grid (%.1f s, 1 thread)"
+                      % (n, w.nx, w.ny, el)}
+
+
+# ----------------------------------------------------------------------------
+# GPU measurement
+# ----------------------------------------------------------------------------
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def device_uuid(torch):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return None
+
+
+def time_steps(torch, lbm, ctx, stream, flush, K, W):
+    """Per-step CUDA-event times (ms) of K steps after W warm-up steps."""
+    with torch.cuda.stream(stream):
+        for _ in range(W):
+            lbm.lbm_step(ctx, 1)
+            flush.zero_()
+        stream.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        torch.cuda._sleep(200_000_000)   # keep the GPU busy while the loop is enqueued
+        for a, b in ev:
+            a.record(stream)
+            lbm.lbm_step(ctx, 1)
+            b.record(stream)
+            flush.zero_()
+        stream.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def make_ctx(lbm, w, precision, audit_every, stream):
+    cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, precision, audit_every)
+    ctx = lbm.lbm_create(cfg, stream)
+    lbm.lbm_set_init(ctx, *[np.ascontiguousarray(a) for a in w.fields()])
+    return ctx
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
+    None when the CUDA sources changed after it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    return rec["dram_bytes_per_launch"] if rec.get("source_hash") == source_hash() else None
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_0908_3749_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def e2e_steps(torch, lbm, ctx, w, K, W):
+    """Steps through the C ABI with host buffers: each step copies the
+    populations in from pinned host memory, runs one step and reads the
+    moments back into pinned host memory. Wall-clock seconds per step."""
+    f = torch.empty((16, w.ny, w.nx), dtype=torch.float32).pin_memory()
+    outs = [torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    fn = f.numpy()
+    on = [o.numpy() for o in outs]
+    lbm.lbm_get_populations(ctx, fn)
+    times = []
+    for k in range(W + K):
+        t0 = time.perf_counter()
+        lbm.lbm_set_populations(ctx, fn, k)
+        lbm.lbm_step(ctx, 1)
+        lbm.lbm_moments(ctx, *on)
+        if k >= W:
+            times.append(time.perf_counter() - t0)
+    return times, f.numel() * 4, sum(o.numel() * 8 for o in outs)
+
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_0908_3749_gb300 import lbm
+    lbm.load()
+    w = workload()
+    cells = w.nx * w.ny
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ctx32 = make_ctx(lbm, w, "fp32", args.audit_every, stream)
+    ctx64 = make_ctx(lbm, w, "fp64", args.audit_every, stream)
+    K, W = args.steps, args.warmup
+
+    # FP64 path (not the headline; measured first, same procedure)
+    t64 = time_steps(torch, lbm, ctx64, stream, flush, K, W)
+
+    # FP32 path: the timed region of the JSON line
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(device_uuid(torch))
+    t32 = time_steps(torch, lbm, ctx32, stream, flush, K, W)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    total32 = sum(t32)
+    total64 = sum(t64)
+    if dist:
+        t = torch.tensor([total32, total64], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total32, total64 = t.tolist()
+
+    # accuracy of the FP32 path against the FP64 path after the same steps
+    m32 = [np.empty((w.ny, w.nx)) for _ in range(4)]
+    m64 = [np.empty((w.ny, w.nx)) for _ in range(4)]
+    lbm.lbm_moments(ctx32, *m32)
+    lbm.lbm_moments(ctx64, *m64)
+    speed = np.sqrt(m64[1] ** 2 + m64[2] ** 2).max()
+    acc = {"rho": float(np.abs(m32[0] - m64[0]).max() / np.abs(m64[0]).max()),
+           "u": float(np.abs(m32[1] - m64[1]).max() / speed),
+           "v": float(np.abs(m32[2] - m64[2]).max() / speed),
+           "T": float(np.abs(m32[3] - m64[3]).max() / np.abs(m64[3]).max())}
+    s32 = lbm.lbm_status(ctx32)
+    s64 = lbm.lbm_status(ctx64)
+
+    e2e_t, h2d, d2h = e2e_steps(torch, lbm, ctx32, w, max(10, K // 4), 3)
+    lbm.lbm_destroy(ctx32)
+    lbm.lbm_destroy(ctx64)
+
+    # Same FP32 step on a grid larger than L2 (the 2048 x 1024 shock-bubble
+    # set-up, 268 MB of traffic per step): the HBM-bound regime.
+    large = None
+    if not args.no_large:
+        import workloads as W
+        wl = W.shock_bubble()
+        ctxl = make_ctx(lbm, wl, "fp32", args.audit_every, stream)
+        tl = time_steps(torch, lbm, ctxl, stream, flush, min(K, 50), W)
+        lbm.lbm_destroy(ctxl)
+        msl = sum(tl) / len(tl)
+        cl = wl.nx * wl.ny
+        gbl = BYTES_PER_CELL["fp32"] * cl / (msl * 1e-3) / 1e9
+        large = {"workload": "shock_bubble_%dx%d" % (wl.nx, wl.ny), "value": cl / (msl * 1e-3),
+                 "unit": UNIT, "ms_per_step": msl, "achieved_gbs": gbl, "steps": len(tl)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    ms32 = total32 / K
+    ms64 = total64 / K
+    gbs = BYTES_PER_CELL["fp32"] * cells / (ms32 * 1e-3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if large:
+        large["frac_of_hbm"] = large["achieved_gbs"] / hbm_peak
+    tflops64 = FLOPS_PER_CELL * cells / (ms64 * 1e-3) / 1e12
+    line = {
+        "metric": METRIC,
+        "value": world * cells * K / (total32 * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms32,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": config_json(w, "fp32", args.audit_every),
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": gbs / hbm_peak, "traffic": traffic_record("k_step<float>"),
+                     "kernel": "k_step<float>",
+                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                     "bytes_per_cell_update": BYTES_PER_CELL["fp32"]},
+        "accuracy_fp32_vs_fp64": acc,
+        "fp64": {"value": world * cells * K / (total64 * 1e-3), "unit": UNIT,
+                 "ms_per_step": ms64, "dtype": "f64",
+                 "roofline": {"bound": "alu", "achieved": tflops64, "peak": FP64_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": tflops64 / FP64_PEAK_TFLOPS,
+                              "peak_source": "nominal FP64 rate (2 DFMA/clk/SM)",
+                              "flops_per_cell_update": FLOPS_PER_CELL,
+                              "traffic": traffic_record("k_step<double>"),
+                              "hbm_frac": BYTES_PER_CELL["fp64"] * cells / (ms64 * 1e-3) / 1e9 / hbm_peak}},
+        "status": {"fp32": list(s32), "fp64": list(s64)},
+        "fp32_large_grid": large,
+        "e2e": {"value": cells / statistics.mean(e2e_t), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "lbm_set_populations(pinned host) + lbm_step(1) + lbm_moments(pinned host)"},
+        "clocks": clk,
+        "gpu_launches": K,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The CPU oracle timed as the reference arm (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    w = workload()
+    cells = w.nx * w.ny
+    oracle_steps(steps=args.warmup)
+    n, el = oracle_steps(steps=args.steps)
+    value = cells * n / el
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n,
+        "warmup": args.warmup, "ms_per_step": el / n * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_json(w, "fp64", 0), "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d full-grid steps of the FP64 numpy oracle, 1 thread" % n},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--audit-every", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_sample is not None:
+        print(json.dumps(oracle_steps(seconds=args.cpu_sample)))
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -51,10 +51,8 @@ SIDES = ("x-", "x+", "y-", "y+")
 # ----------------------------------------------------------------------------
 def conserved_from_state(rho, u, v, T):
     """(rho, j_x, j_y, e) of a state (rho, u, v, T) under reading R1."""
-    rho = np.asarray(rho, dtype=np.float64)
-    u = np.asarray(u, dtype=np.float64)
-    v = np.asarray(v, dtype=np.float64)
-    T = np.asarray(T, dtype=np.float64)
+    dt = np.result_type(rho, u, v, T, np.float64)   # float64 (or wider)
+    rho, u, v, T = (np.asarray(q, dtype=dt) for q in (rho, u, v, T))
     return rho, rho * u, rho * v, rho * T + 0.5 * rho * (u * u + v * v)
 
 
@@ -64,7 +62,7 @@ def moment_equilibria(rho, jx, jy, e):
     Rows 1-4 are the conserved moments themselves; rows 12, 15, 16 are zero.
     P = e - |j|^2/(2 rho) by reading R1.
     """
-    rho = np.asarray(rho, dtype=np.float64)
+    rho = np.asarray(rho, dtype=np.result_type(rho, np.float64))
     jx2 = jx * jx
     jy2 = jy * jy
     jsq = jx2 + jy2

@@ -1,0 +1,923 @@
+// lbm_core.cu -- 2D grid path of the MRT-FD D2V16 scheme: kernels and the C ABI
+// declared in include/lbm.h.
+//
+// Data layout in HBM: populations are structure-of-arrays,
+//   f[i][y][x] at offset i * plane + y * pitch + x,
+// pitch = nx rounded up to 32 elements (rows start on 128-byte (FP32) or
+// 256-byte (FP64) boundaries), plane = ny * pitch. There is no ghost ring in
+// memory: the step computes boundary ghosts on the fly from the time-n
+// interior (or reads the fixed Dirichlet ghosts), so one launch per step
+// carries the whole update. Two buffers alternate (time n -> n+1).
+//
+// One step (one launch of k_step) per node:
+//   load the node's 16 populations -> 4-point group transforms -> conserved
+//   moments -> Eq. 14 equilibria -> relaxation folded into the back-map (Eq. 3)
+//   -> f(1 - cx^2 - cy^2) + collision -> Lax-Wendroff neighbour terms of
+//   Eq. A.1b (12 x-neighbours, 12 y-neighbours, ghosts at the domain edge)
+//   -> store; epilogue: watchdog flags and, every audit_every steps, block
+//   partial sums of (rho, j, e) in FP64 with a fixed-order final pass done by
+//   the last block to finish (no floating-point atomics).
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstddef>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "d2v16.cuh"
+
+using namespace d2v16;
+
+namespace {
+
+constexpr int GRAPH_CHUNK = 64;  // steps per captured graph (even)
+constexpr unsigned long long NONE = ~0ull;
+// Thread-block shapes: FP32 32 x 8 (memory-bound, more warps in flight),
+// FP64 32 x 4 (FP64-ALU-bound; smaller blocks balance the SMs better).
+template <typename R> struct Shape;
+template <> struct Shape<float> { static constexpr int X = 32, Y = 8; };
+template <> struct Shape<double> { static constexpr int X = 32, Y = 4; };
+constexpr int AUX_X = 32, AUX_Y = 8, AUX_N = AUX_X * AUX_Y;  // init / moments / audit
+
+// Device-resident status block of one context.
+struct DevStatus {
+  unsigned long long blocks_done; // step blocks finished; time level = blocks_done / nblocks
+  unsigned int arrive_audit;      // blocks finished in a standalone audit
+  unsigned int pad;
+  unsigned long long first_bad;   // first level with non-finite / rho <= 0
+  unsigned long long first_negT;  // first level with T <= 0
+  unsigned long long audit_count; // fused audits written so far
+  double audit_now[4];            // result of the standalone audit
+  double audit_totals[LBM_AUDIT_RING][4];
+  long long audit_steps[LBM_AUDIT_RING];
+};
+
+template <typename R>
+struct StepArgs {
+  Coeffs<R> K;
+  int nx, ny;
+  long long pitch, plane;
+  int bc[4];          // x-, x+, y-, y+
+  R wall[4][3];       // (u, v, T) of LBM_BC_WALL sides
+  const R* geq;       // [4][16] Dirichlet ghost populations
+  DevStatus* st;
+  double* partial;    // [nblocks][4] audit scratch
+  int audit_every;
+  int nblocks;
+  double area;        // dx * dy
+};
+
+// ---------------------------------------------------------------------------
+// Fixed-order FP64 reductions of four sums (bitwise reproducible)
+// ---------------------------------------------------------------------------
+// Warp sum of v[0..3] by a transposing butterfly: the first two exchange
+// levels halve the number of live sums, so a lane does 6 additions instead of
+// 20. Afterwards lanes 0, 8, 16, 24 hold the warp totals of sums 0, 1, 2, 3.
+__device__ __forceinline__ double warp_sum4(const double v[4], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const double s0 = h16 ? v[0] : v[2], s1 = h16 ? v[1] : v[3];
+  double k0 = (h16 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, s0, 16);
+  double k1 = (h16 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, s1, 16);
+  double k = (h8 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
+// Block sum of v[0..3] (N threads); threads 0..3 return sums 0..3.
+template <int N>
+__device__ __forceinline__ double block_sum4(const double v[4], double (*sm)[4]) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const double k = warp_sum4(v, lane);
+  if ((lane & 7) == 0) sm[warp][lane >> 3] = k;
+  __syncthreads();
+  double s = 0.0;
+  if (t < 4)
+    for (int w = 0; w < N / 32; ++w) s += sm[w][t];
+  return s;
+}
+
+// Sum of partial[b][q] over b by all N threads of one block, in a fixed
+// order: thread t takes q = t % 4 and blocks b = t/4, t/4 + N/4, ...; then a
+// fixed tree. Threads 0..3 return the totals of q = 0..3.
+template <int N>
+__device__ __forceinline__ double final_sum4(const double* partial, int nblocks,
+                                             double (*sm)[4]) {
+  constexpr int G = N / 4;
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int q = t & 3, j = t >> 2;
+  double s = 0.0;
+#pragma unroll 4
+  for (int b = j; b < nblocks; b += G) s += __ldcg(partial + 4 * b + q);
+  sm[j][q] = s;
+  __syncthreads();
+#pragma unroll
+  for (int stride = G / 2; stride > 0; stride >>= 1) {
+    if (j < stride) sm[j][q] += sm[j + stride][q];
+    __syncthreads();
+  }
+  return t < 4 ? sm[0][t] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Boundary ghosts
+// ---------------------------------------------------------------------------
+template <typename R, typename Off>
+__device__ __forceinline__ Cons<R> load_cons(const R* __restrict__ fin, Off plane, Off idx) {
+  R f[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) f[i] = fin[i * plane + idx];
+  Groups<R> d;
+  transform(f, d);
+  return conserved(d);
+}
+
+// Ghost populations outside `side` of the node with conserved moments `own`.
+// `inward` is the index of the next node inwards (EXTRAP), `has_inward`
+// false when the grid is one node deep in that direction.
+template <typename R, typename Off>
+__device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict__ fin,
+                                      Off plane, int side, Cons<R> own, Off inward,
+                                      bool has_inward, R g[16]) {
+  const int kind = A.bc[side];
+  if (kind == LBM_BC_EQ) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) g[i] = A.geq[side * 16 + i];
+    return;
+  }
+  Cons<R> s = own;
+  if (kind == LBM_BC_REFLECT) {
+    if (side < 2) s.jx = -s.jx; else s.jy = -s.jy;
+  } else if (kind == LBM_BC_WALL) {
+    const R u = A.wall[side][0], v = A.wall[side][1], T = A.wall[side][2];
+    s.jx = own.rho * u;
+    s.jy = own.rho * v;
+    s.e = own.rho * T + R(0.5) * own.rho * (u * u + v * v);
+  } else {  // LBM_BC_EXTRAP
+    const Cons<R> in = has_inward ? load_cons(fin, plane, inward) : own;
+    const R r1 = recip(own.rho), r2 = recip(in.rho);
+    const R u1 = own.jx * r1, v1 = own.jy * r1, u2 = in.jx * r2, v2 = in.jy * r2;
+    const R T1 = own.e * r1 - R(0.5) * (u1 * u1 + v1 * v1);
+    const R T2 = in.e * r2 - R(0.5) * (u2 * u2 + v2 * v2);
+    R rho = R(2) * own.rho - in.rho, u = R(2) * u1 - u2, v = R(2) * v1 - v2,
+      T = R(2) * T1 - T2;
+    if (!(rho > R(0) && T > R(0))) {
+      rho = own.rho; u = u1; v = v1; T = T1;
+    }
+    s.rho = rho;
+    s.jx = rho * u;
+    s.jy = rho * v;
+    s.e = rho * T + R(0.5) * rho * (u * u + v * v);
+  }
+  feq(A.K, s.rho, s.jx, s.jy, s.e, g);
+}
+
+// ---------------------------------------------------------------------------
+// The fused step
+// ---------------------------------------------------------------------------
+// Off: unsigned (32-bit element offsets, grids with 16 * plane < 2^32) or
+// long long. One thread per node.
+template <typename R, typename Off>
+__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y)
+    k_step(const R* __restrict__ fin, R* __restrict__ fout, const StepArgs<R> A) {
+  constexpr int BXD = Shape<R>::X, BYD = Shape<R>::Y, N = BXD * BYD;
+  __shared__ double sm[N / 4][4];
+  __shared__ unsigned long long s_step;
+  __shared__ int s_last;
+  const int t = threadIdx.y * BXD + threadIdx.x;
+  if (t == 0) {
+    const unsigned long long done = *(volatile unsigned long long*)&A.st->blocks_done;
+    s_step = done / (unsigned long long)A.nblocks;
+  }
+  __syncthreads();
+  const unsigned long long step = s_step;
+  const bool audit = A.audit_every > 0 && (step % (unsigned long long)A.audit_every) == 0;
+
+  const int x = blockIdx.x * BXD + threadIdx.x;
+  const int y = blockIdx.y * BYD + threadIdx.y;
+  const bool active = x < A.nx && y < A.ny;
+  double tot[4] = {0.0, 0.0, 0.0, 0.0};
+  bool bad = false, negT = false;
+
+  if (active) {
+    const Off P = (Off)A.plane, pitch = (Off)A.pitch;
+    const Off c = (Off)y * pitch + (Off)x;
+    R f[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) f[i] = fin[i * P + c];
+    Groups<R> d;
+    transform(f, d);
+    const Cons<R> m = conserved(d);
+    R acc[16];
+    const R press = collide(A.K, d, m, acc);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = A.K.a0[i] * f[i] + acc[i];
+
+    bad = !(m.rho > R(0)) || !isfinite(m.rho + m.jx + m.jy + m.e);
+    negT = !bad && !(press > R(0));
+    if (audit) {
+      tot[0] = (double)m.rho; tot[1] = (double)m.jx;
+      tot[2] = (double)m.jy;  tot[3] = (double)m.e;
+    }
+
+    // x- neighbour (west)
+    if (x > 0 || A.bc[0] == LBM_BC_PERIODIC) {
+      const Off n = (x > 0) ? c - 1 : c + (Off)(A.nx - 1);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_x(i)) acc[i] += A.K.aW[i] * fin[i * P + n];
+    } else {
+      R g[16];
+      ghost(A, fin, P, 0, m, c + 1, A.nx > 1, g);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_x(i)) acc[i] += A.K.aW[i] * g[i];
+    }
+    // x+ neighbour (east)
+    if (x < A.nx - 1 || A.bc[1] == LBM_BC_PERIODIC) {
+      const Off n = (x < A.nx - 1) ? c + 1 : c - (Off)(A.nx - 1);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_x(i)) acc[i] += A.K.aE[i] * fin[i * P + n];
+    } else {
+      R g[16];
+      ghost(A, fin, P, 1, m, c - 1, A.nx > 1, g);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_x(i)) acc[i] += A.K.aE[i] * g[i];
+    }
+    // y- neighbour (south)
+    if (y > 0 || A.bc[2] == LBM_BC_PERIODIC) {
+      const Off n = (y > 0) ? c - pitch : c + (Off)(A.ny - 1) * pitch;
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_y(i)) acc[i] += A.K.aS[i] * fin[i * P + n];
+    } else {
+      R g[16];
+      ghost(A, fin, P, 2, m, c + pitch, A.ny > 1, g);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_y(i)) acc[i] += A.K.aS[i] * g[i];
+    }
+    // y+ neighbour (north)
+    if (y < A.ny - 1 || A.bc[3] == LBM_BC_PERIODIC) {
+      const Off n = (y < A.ny - 1) ? c + pitch : c - (Off)(A.ny - 1) * pitch;
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_y(i)) acc[i] += A.K.aN[i] * fin[i * P + n];
+    } else {
+      R g[16];
+      ghost(A, fin, P, 3, m, c - pitch, A.ny > 1, g);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_y(i)) acc[i] += A.K.aN[i] * g[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) fout[i * P + c] = acc[i];
+  }
+
+  // Watchdog: one atomic per warp that saw a bad node.
+  const unsigned badm = __ballot_sync(0xffffffffu, bad);
+  const unsigned negm = __ballot_sync(0xffffffffu, negT);
+  if ((t & 31) == 0) {
+    if (badm) atomicMin(&A.st->first_bad, step);
+    if (negm) atomicMin(&A.st->first_negT, step);
+  }
+
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (!audit) {
+    if (t == 0) atomicAdd(&A.st->blocks_done, 1ull);
+    return;
+  }
+  const double bs = block_sum4<N>(tot, sm);
+  if (t < 4) A.partial[4 * bid + t] = bs;
+  __syncthreads();
+  if (t == 0) {
+    __threadfence();
+    const unsigned long long prev = atomicAdd(&A.st->blocks_done, 1ull);
+    s_last = (prev + 1 == (step + 1) * (unsigned long long)A.nblocks);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    const double tot4 = final_sum4<N>(A.partial, A.nblocks, sm);
+    if (t < 4) {
+      const unsigned long long slot = A.st->audit_count % LBM_AUDIT_RING;
+      A.st->audit_totals[slot][t] = tot4 * A.area;
+    }
+    __syncthreads();
+    if (t == 0) {
+      const unsigned long long slot = A.st->audit_count % LBM_AUDIT_RING;
+      A.st->audit_steps[slot] = (long long)step;
+      A.st->audit_count += 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state, moments out, standalone audit, Dirichlet ghosts
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_init(R* __restrict__ f, const double* __restrict__ rho,
+                       const double* __restrict__ u, const double* __restrict__ v,
+                       const double* __restrict__ T, const Coeffs<double> K,
+                       int nx, int ny, long long pitch, long long plane) {
+  const int x = blockIdx.x * AUX_X + threadIdx.x;
+  const int y = blockIdx.y * AUX_Y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const long long k = (long long)y * nx + x;
+  const double r = rho[k], uu = u[k], vv = v[k];
+  double g[16];
+  feq(K, r, r * uu, r * vv, r * T[k] + 0.5 * r * (uu * uu + vv * vv), g);
+  const long long c = (long long)y * pitch + x;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) f[i * plane + c] = (R)g[i];
+}
+
+template <typename R>
+__global__ void k_moments(const R* __restrict__ f, double* rho, double* u,
+                          double* v, double* T, int nx, int ny, long long pitch,
+                          long long plane) {
+  const int x = blockIdx.x * AUX_X + threadIdx.x;
+  const int y = blockIdx.y * AUX_Y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const long long c = (long long)y * pitch + x;
+  double g[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) g[i] = (double)f[i * plane + c];
+  Groups<double> d;
+  transform(g, d);
+  const Cons<double> m = conserved(d);
+  const double r = 1.0 / m.rho;
+  const double uu = m.jx * r, vv = m.jy * r;
+  const long long k = (long long)y * nx + x;
+  if (rho) rho[k] = m.rho;
+  if (u) u[k] = uu;
+  if (v) v[k] = vv;
+  if (T) T[k] = m.e * r - 0.5 * (uu * uu + vv * vv);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(AUX_N) k_audit(const R* __restrict__ f, int nx,
+                                                 int ny, long long pitch,
+                                                 long long plane, double area,
+                                                 DevStatus* st, double* partial) {
+  __shared__ double sm[AUX_N / 4][4];
+  __shared__ int s_last;
+  const int x = blockIdx.x * AUX_X + threadIdx.x;
+  const int y = blockIdx.y * AUX_Y + threadIdx.y;
+  const int t = threadIdx.y * AUX_X + threadIdx.x;
+  double tot[4] = {0.0, 0.0, 0.0, 0.0};
+  if (x < nx && y < ny) {
+    const long long c = (long long)y * pitch + x;
+    double g[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) g[i] = (double)f[i * plane + c];
+    Groups<double> d;
+    transform(g, d);
+    const Cons<double> m = conserved(d);
+    tot[0] = m.rho; tot[1] = m.jx; tot[2] = m.jy; tot[3] = m.e;
+  }
+  const int nblocks = gridDim.x * gridDim.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const double bs = block_sum4<AUX_N>(tot, sm);
+  if (t < 4) partial[4 * bid + t] = bs;
+  __syncthreads();
+  if (t == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&st->arrive_audit, 1u);
+    s_last = (prev == (unsigned)nblocks - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    const double tot4 = final_sum4<AUX_N>(partial, nblocks, sm);
+    if (t < 4) st->audit_now[t] = tot4 * area;
+    if (t == 0) st->arrive_audit = 0;
+  }
+}
+
+template <typename R>
+__global__ void k_ghost_eq(R* g, const Coeffs<double> K, const double* states) {
+  const int side = threadIdx.x;
+  if (side >= 4) return;
+  const double r = states[4 * side], u = states[4 * side + 1],
+               v = states[4 * side + 2], T = states[4 * side + 3];
+  double out[16];
+  feq(K, r, r * u, r * v, r * T + 0.5 * r * (u * u + v * v), out);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) g[16 * side + i] = (R)out[i];
+}
+
+// ---------------------------------------------------------------------------
+// Host-side constants
+// ---------------------------------------------------------------------------
+// Gauss-Jordan inverse with partial pivoting in long double (n <= 4).
+bool invert(int n, const double* a, double* out) {
+  long double m[4][8];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j)
+      m[i][j] = j < n ? (long double)a[i * n + j] : (long double)(j - n == i);
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabsl(m[r][c]) > fabsl(m[p][c])) p = r;
+    if (m[p][c] == 0.0L) return false;
+    for (int j = 0; j < 2 * n; ++j) { long double t = m[c][j]; m[c][j] = m[p][j]; m[p][j] = t; }
+    const long double piv = m[c][c];
+    for (int j = 0; j < 2 * n; ++j) m[c][j] /= piv;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const long double fac = m[r][c];
+      for (int j = 0; j < 2 * n; ++j) m[r][j] -= fac * m[c][j];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) out[i * n + j] = (double)m[i][n + j];
+  return true;
+}
+
+bool build_coeffs(const lbm_config& cfg, Coeffs<double>& K) {
+  double m0[16], mx[16], my[16], mc[4], ms[4];
+  for (int r = 0; r < 4; ++r)
+    for (int g = 0; g < 4; ++g) {
+      m0[4 * r + g] = b0(r, g);
+      mx[4 * r + g] = bx(r, g);
+      my[4 * r + g] = by(r, g);
+    }
+  for (int r = 0; r < 2; ++r)
+    for (int g = 0; g < 2; ++g) {
+      mc[2 * r + g] = bc2(r, g);
+      ms[2 * r + g] = bs2(r, g);
+    }
+  double i0[16], ix[16], iy[16], ic[4], is[4];
+  if (!invert(4, m0, i0) || !invert(4, mx, ix) || !invert(4, my, iy) ||
+      !invert(2, mc, ic) || !invert(2, ms, is))
+    return false;
+  const double sx[4] = {0.5, 0.5, 0.25, 0.25};
+  for (int g = 0; g < 4; ++g)
+    for (int c = 0; c < 4; ++c) {
+      K.E0[g][c] = 0.25 * i0[g * 4 + c];
+      K.EX[g][c] = sx[g] * ix[g * 4 + c];
+      K.EY[g][c] = sx[g] * iy[g * 4 + c];
+    }
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) {
+      K.EC[r][c] = 0.25 * ic[r * 2 + c];
+      K.ES[r][c] = 0.25 * is[r * 2 + c];
+    }
+  double w[17];
+  for (int k = 1; k <= 16; ++k) w[k] = -cfg.dt * cfg.s[k - 1];
+  const int cx[3] = {7, 9, 15}, cy[3] = {8, 10, 16};
+  for (int g = 0; g < 4; ++g) {
+    K.K0[g][0] = K.E0[g][2] * w[11];
+    K.K0[g][1] = K.E0[g][3] * w[12];
+    for (int c = 0; c < 3; ++c) {
+      K.KX[g][c] = K.EX[g][c + 1] * w[cx[c]];
+      K.KY[g][c] = K.EY[g][c + 1] * w[cy[c]];
+    }
+  }
+  for (int r = 0; r < 2; ++r) {
+    K.KC[r][0] = K.EC[r][0] * w[5];
+    K.KC[r][1] = K.EC[r][1] * w[13];
+    K.KS[r][0] = K.ES[r][0] * w[6];
+    K.KS[r][1] = K.ES[r][1] * w[14];
+  }
+  for (int i = 0; i < 16; ++i) {
+    const double ax = vel_x(i) * cfg.dt / cfg.dx, ay = vel_y(i) * cfg.dt / cfg.dy;
+    K.a0[i] = 1.0 - ax * ax - ay * ay;
+    K.aE[i] = 0.5 * (ax * ax - ax);
+    K.aW[i] = 0.5 * (ax * ax + ax);
+    K.aN[i] = 0.5 * (ay * ay - ay);
+    K.aS[i] = 0.5 * (ay * ay + ay);
+  }
+  return true;
+}
+
+template <typename R>
+Coeffs<R> cast_coeffs(const Coeffs<double>& K) {
+  Coeffs<R> o;
+  const double* s = reinterpret_cast<const double*>(&K);
+  R* d = reinterpret_cast<R*>(&o);
+  for (size_t k = 0; k < sizeof(Coeffs<double>) / sizeof(double); ++k) d[k] = (R)s[k];
+  return o;
+}
+
+thread_local std::string g_create_error = "no error";
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct lbm_ctx {
+  lbm_config cfg;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int esize = 8;
+  long long pitch = 0, plane = 0;
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* geq = nullptr;
+  DevStatus* st = nullptr;
+  double* partial = nullptr;
+  double* staging = nullptr;
+  int nblocks = 0;      // blocks of one step launch
+  dim3 grid, aux_grid;  // step grid; init / moments / audit grid
+  bool wide = false;    // 64-bit element offsets needed
+  Coeffs<double> Kd;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::string err = "no error";
+};
+
+namespace {
+
+int fail(lbm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg; else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+}
+
+#define CK(ctx, call)                                       \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+template <typename R>
+StepArgs<R> make_args(lbm_ctx* c) {
+  StepArgs<R> A;
+  A.K = cast_coeffs<R>(c->Kd);
+  A.nx = c->cfg.nx;
+  A.ny = c->cfg.ny;
+  A.pitch = c->pitch;
+  A.plane = c->plane;
+  for (int s = 0; s < 4; ++s) {
+    A.bc[s] = c->cfg.bc[s].kind;
+    A.wall[s][0] = (R)c->cfg.bc[s].u;
+    A.wall[s][1] = (R)c->cfg.bc[s].v;
+    A.wall[s][2] = (R)c->cfg.bc[s].T;
+  }
+  A.geq = (const R*)c->geq;
+  A.st = c->st;
+  A.partial = c->partial;
+  A.audit_every = c->cfg.audit_every;
+  A.nblocks = c->nblocks;
+  A.area = c->cfg.dx * c->cfg.dy;
+  return A;
+}
+
+int launch_step(lbm_ctx* c, cudaStream_t s, int from) {
+  const int to = 1 - from;
+  if (c->esize == 8) {
+    const dim3 blk(Shape<double>::X, Shape<double>::Y);
+    const double* fi = (const double*)c->f[from];
+    double* fo = (double*)c->f[to];
+    if (c->wide) k_step<double, long long><<<c->grid, blk, 0, s>>>(fi, fo, make_args<double>(c));
+    else k_step<double, unsigned><<<c->grid, blk, 0, s>>>(fi, fo, make_args<double>(c));
+  } else {
+    const dim3 blk(Shape<float>::X, Shape<float>::Y);
+    const float* fi = (const float*)c->f[from];
+    float* fo = (float*)c->f[to];
+    if (c->wide) k_step<float, long long><<<c->grid, blk, 0, s>>>(fi, fo, make_args<float>(c));
+    else k_step<float, unsigned><<<c->grid, blk, 0, s>>>(fi, fo, make_args<float>(c));
+  }
+  CK(c, cudaGetLastError());
+  return LBM_OK;
+}
+
+int ensure_graph(lbm_ctx* c, int from) {
+  if (c->graph[from]) return LBM_OK;
+  cudaGraph_t g;
+  CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int f = from, rc = LBM_OK;
+  for (int k = 0; k < GRAPH_CHUNK && rc == LBM_OK; ++k) {
+    rc = launch_step(c, c->stream, f);
+    f = 1 - f;
+  }
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (rc != LBM_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->graph[from], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  return LBM_OK;
+}
+
+int reset_status(lbm_ctx* c, unsigned long long step) {
+  DevStatus h;
+  memset(&h, 0, offsetof(DevStatus, audit_totals));
+  h.blocks_done = step * (unsigned long long)c->nblocks;
+  h.first_bad = NONE;
+  h.first_negT = NONE;
+  CK(c, cudaMemcpyAsync(c->st, &h, offsetof(DevStatus, audit_totals),
+                        cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
+  if (!out) return fail(nullptr, LBM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, LBM_ERR_INVALID, "cfg is NULL");
+  const lbm_config& C = *cfg;
+  if (C.nx < 1 || C.ny < 1) return fail(nullptr, LBM_ERR_INVALID, "nx and ny must be >= 1");
+  if ((long long)C.nx * C.ny > (1ll << 31))
+    return fail(nullptr, LBM_ERR_INVALID, "grid too large");
+  if (!finite_pos(C.dx) || !finite_pos(C.dy) || !finite_pos(C.dt))
+    return fail(nullptr, LBM_ERR_INVALID, "dx, dy, dt must be finite and > 0");
+  for (int k = 0; k < 16; ++k)
+    if (!std::isfinite(C.s[k]) || C.s[k] < 0.0)
+      return fail(nullptr, LBM_ERR_INVALID, "relaxation rates must be finite and >= 0");
+  if (6.0 * C.dt / C.dx > 1.0 || 6.0 * C.dt / C.dy > 1.0)
+    return fail(nullptr, LBM_ERR_INVALID, "Courant number 6 dt / dx exceeds 1");
+  if (C.internal_dof != 0)
+    return fail(nullptr, LBM_ERR_UNSUPPORTED,
+                "internal_dof != 0: the D2V16 moment set fixes gamma = 2");
+  if (C.precision != LBM_FP64 && C.precision != LBM_FP32)
+    return fail(nullptr, LBM_ERR_UNSUPPORTED, "precision not built for the 2D grid path");
+  if (C.audit_every < 0) return fail(nullptr, LBM_ERR_INVALID, "audit_every < 0");
+  for (int s = 0; s < 4; ++s) {
+    const lbm_bc& b = C.bc[s];
+    if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_WALL)
+      return fail(nullptr, LBM_ERR_INVALID, "bad boundary kind");
+    if (b.kind == LBM_BC_EQ && !(finite_pos(b.rho) && finite_pos(b.T) &&
+                                 std::isfinite(b.u) && std::isfinite(b.v)))
+      return fail(nullptr, LBM_ERR_INVALID, "Dirichlet state needs rho > 0, T > 0");
+    if (b.kind == LBM_BC_WALL && !(finite_pos(b.T) && std::isfinite(b.u) && std::isfinite(b.v)))
+      return fail(nullptr, LBM_ERR_INVALID, "wall state needs T > 0");
+  }
+  if ((C.bc[0].kind == LBM_BC_PERIODIC) != (C.bc[1].kind == LBM_BC_PERIODIC) ||
+      (C.bc[2].kind == LBM_BC_PERIODIC) != (C.bc[3].kind == LBM_BC_PERIODIC))
+    return fail(nullptr, LBM_ERR_INVALID, "periodic must be set on both opposite sides");
+
+  lbm_ctx* c = new lbm_ctx();
+  c->cfg = C;
+  c->esize = C.precision == LBM_FP64 ? 8 : 4;
+  if (!build_coeffs(C, c->Kd)) {
+    delete c;
+    return fail(nullptr, LBM_ERR_INVALID, "singular moment block");
+  }
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreate(&c->stream);  // blocking: ordered with the default stream
+    c->own_stream = true;
+  }
+  c->pitch = ((long long)C.nx + 31) / 32 * 32;
+  c->plane = c->pitch * C.ny;
+  const int bx = c->esize == 8 ? Shape<double>::X : Shape<float>::X;
+  const int by = c->esize == 8 ? Shape<double>::Y : Shape<float>::Y;
+  c->grid = dim3((C.nx + bx - 1) / bx, (C.ny + by - 1) / by);
+  c->aux_grid = dim3((C.nx + AUX_X - 1) / AUX_X, (C.ny + AUX_Y - 1) / AUX_Y);
+  c->nblocks = (int)(c->grid.x * c->grid.y);
+  c->wide = 16ll * c->plane >= (1ll << 32);
+  const int npartial = std::max(c->nblocks, (int)(c->aux_grid.x * c->aux_grid.y));
+  const size_t fbytes = (size_t)16 * c->plane * c->esize;
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&c->f[b], fbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->geq, 64 * c->esize);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->st, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->partial, sizeof(double) * 4 * npartial);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&c->staging, sizeof(double) * 4 * (size_t)C.nx * C.ny);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(c->f[b], 0, fbytes, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream);
+  if (e == cudaSuccess) {
+    double states[16];
+    double* dstates = nullptr;
+    for (int s = 0; s < 4; ++s) {
+      const bool eq = C.bc[s].kind == LBM_BC_EQ;
+      states[4 * s] = eq ? C.bc[s].rho : 1.0;
+      states[4 * s + 1] = eq ? C.bc[s].u : 0.0;
+      states[4 * s + 2] = eq ? C.bc[s].v : 0.0;
+      states[4 * s + 3] = eq ? C.bc[s].T : 1.0;
+    }
+    e = cudaMalloc((void**)&dstates, sizeof(states));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dstates, states, sizeof(states), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+      if (c->esize == 8)
+        k_ghost_eq<double><<<1, 32, 0, c->stream>>>((double*)c->geq, c->Kd, dstates);
+      else
+        k_ghost_eq<float><<<1, 32, 0, c->stream>>>((float*)c->geq, c->Kd, dstates);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (dstates) cudaFree(dstates);
+  }
+  if (e != cudaSuccess) {
+    const int rc = cuda_fail(nullptr, e, "lbm_create");
+    lbm_destroy(c);
+    return rc;
+  }
+  if (reset_status(c, 0) != LBM_OK) {
+    g_create_error = c->err;
+    lbm_destroy(c);
+    return LBM_ERR_CUDA;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_set_init(lbm_ctx* c, const double* rho, const double* u, const double* v,
+                 const double* T, int on_device) {
+  if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+  if (!rho || !u || !v || !T) return fail(c, LBM_ERR_INVALID, "NULL field");
+  const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+  const double* p[4] = {rho, u, v, T};
+  if (!on_device) {
+    for (int k = 0; k < 4; ++k) {
+      CK(c, cudaMemcpyAsync(c->staging + k * n, p[k], n * sizeof(double),
+                            cudaMemcpyHostToDevice, c->stream));
+      p[k] = c->staging + k * n;
+    }
+  }
+  const dim3 blk(AUX_X, AUX_Y);
+  c->cur = 0;
+  if (c->esize == 8)
+    k_init<double><<<c->aux_grid, blk, 0, c->stream>>>((double*)c->f[0], p[0], p[1], p[2], p[3],
+                                                    c->Kd, c->cfg.nx, c->cfg.ny, c->pitch, c->plane);
+  else
+    k_init<float><<<c->aux_grid, blk, 0, c->stream>>>((float*)c->f[0], p[0], p[1], p[2], p[3],
+                                                   c->Kd, c->cfg.nx, c->cfg.ny, c->pitch, c->plane);
+  CK(c, cudaGetLastError());
+  return reset_status(c, 0);
+}
+
+int lbm_step(lbm_ctx* c, long long nsteps) {
+  if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+  if (nsteps < 0) return fail(c, LBM_ERR_INVALID, "nsteps < 0");
+  while (nsteps >= GRAPH_CHUNK) {
+    int rc = ensure_graph(c, c->cur);
+    if (rc != LBM_OK) return rc;
+    CK(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+    nsteps -= GRAPH_CHUNK;
+  }
+  for (; nsteps > 0; --nsteps) {
+    int rc = launch_step(c, c->stream, c->cur);
+    if (rc != LBM_OK) return rc;
+    c->cur = 1 - c->cur;
+  }
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx* c, double* rho, double* u, double* v, double* T, int on_device) {
+  if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+  const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+  double* d[4] = {rho, u, v, T};
+  double* h[4] = {rho, u, v, T};
+  if (!on_device)
+    for (int k = 0; k < 4; ++k) d[k] = h[k] ? c->staging + k * n : nullptr;
+  const dim3 blk(AUX_X, AUX_Y);
+  if (c->esize == 8)
+    k_moments<double><<<c->aux_grid, blk, 0, c->stream>>>((const double*)c->f[c->cur], d[0], d[1],
+                                                       d[2], d[3], c->cfg.nx, c->cfg.ny,
+                                                       c->pitch, c->plane);
+  else
+    k_moments<float><<<c->aux_grid, blk, 0, c->stream>>>((const float*)c->f[c->cur], d[0], d[1],
+                                                      d[2], d[3], c->cfg.nx, c->cfg.ny,
+                                                      c->pitch, c->plane);
+  CK(c, cudaGetLastError());
+  if (!on_device) {
+    for (int k = 0; k < 4; ++k)
+      if (h[k])
+        CK(c, cudaMemcpyAsync(h[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx* c) {
+  if (!c) return LBM_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int k = 0; k < 2; ++k) {
+    if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+    if (c->f[k]) cudaFree(c->f[k]);
+  }
+  if (c->geq) cudaFree(c->geq);
+  if (c->st) cudaFree(c->st);
+  if (c->partial) cudaFree(c->partial);
+  if (c->staging) cudaFree(c->staging);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return LBM_OK;
+}
+
+int lbm_audit(lbm_ctx* c, double totals[4]) {
+  if (!c || !totals) return fail(c, LBM_ERR_INVALID, "NULL argument");
+  const dim3 blk(AUX_X, AUX_Y);
+  const double area = c->cfg.dx * c->cfg.dy;
+  if (c->esize == 8)
+    k_audit<double><<<c->aux_grid, blk, 0, c->stream>>>((const double*)c->f[c->cur], c->cfg.nx,
+                                                     c->cfg.ny, c->pitch, c->plane, area,
+                                                     c->st, c->partial);
+  else
+    k_audit<float><<<c->aux_grid, blk, 0, c->stream>>>((const float*)c->f[c->cur], c->cfg.nx,
+                                                    c->cfg.ny, c->pitch, c->plane, area,
+                                                    c->st, c->partial);
+  CK(c, cudaGetLastError());
+  CK(c, cudaMemcpyAsync(totals, c->st->audit_now, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_audit_log(lbm_ctx* c, double* totals, long long* steps, int max_entries, int* count) {
+  if (!c || !count || max_entries < 0) return fail(c, LBM_ERR_INVALID, "bad argument");
+  std::vector<DevStatus> h(1);
+  CK(c, cudaMemcpyAsync(h.data(), c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const DevStatus& s = h[0];
+  const unsigned long long n = s.audit_count < LBM_AUDIT_RING ? s.audit_count : LBM_AUDIT_RING;
+  const unsigned long long first = s.audit_count - n;
+  int k = 0;
+  for (unsigned long long a = first; a < s.audit_count && k < max_entries; ++a, ++k) {
+    const unsigned long long slot = a % LBM_AUDIT_RING;
+    if (totals)
+      for (int q = 0; q < 4; ++q) totals[4 * k + q] = s.audit_totals[slot][q];
+    if (steps) steps[k] = s.audit_steps[slot];
+  }
+  *count = k;
+  return LBM_OK;
+}
+
+int lbm_status(lbm_ctx* c, long long* first_bad_step, long long* first_negT_step) {
+  if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+  DevStatus h;
+  CK(c, cudaMemcpyAsync(&h, c->st, offsetof(DevStatus, audit_totals), cudaMemcpyDeviceToHost,
+                        c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const long long bad = h.first_bad == NONE ? -1 : (long long)h.first_bad;
+  const long long neg = h.first_negT == NONE ? -1 : (long long)h.first_negT;
+  if (first_bad_step) *first_bad_step = bad;
+  if (first_negT_step) *first_negT_step = neg;
+  if (bad >= 0) {
+    c->err = "state non-finite or rho <= 0 at time level " + std::to_string(bad);
+    return LBM_ERR_NONFINITE;
+  }
+  return LBM_OK;
+}
+
+long long lbm_step_count(lbm_ctx* c) {
+  if (!c) return -1;
+  unsigned long long s = 0;
+  if (cudaMemcpyAsync(&s, &c->st->blocks_done, sizeof(s), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return -1;
+  return (long long)(s / (unsigned long long)c->nblocks);
+}
+
+int lbm_get_populations(lbm_ctx* c, void* f, long long* step, int on_device) {
+  if (!c || !f) return fail(c, LBM_ERR_INVALID, "NULL argument");
+  const size_t w = (size_t)c->cfg.nx * c->esize;
+  CK(c, cudaMemcpy2DAsync(f, w, c->f[c->cur], (size_t)c->pitch * c->esize, w,
+                          (size_t)16 * c->cfg.ny,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          c->stream));
+  if (step) {
+    unsigned long long s = 0;
+    CK(c, cudaMemcpyAsync(&s, &c->st->blocks_done, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *step = (long long)(s / (unsigned long long)c->nblocks);
+  } else if (!on_device) {
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* c, const void* f, long long step, int on_device) {
+  if (!c || !f || step < 0) return fail(c, LBM_ERR_INVALID, "bad argument");
+  const size_t w = (size_t)c->cfg.nx * c->esize;
+  c->cur = 0;
+  CK(c, cudaMemcpy2DAsync(c->f[0], (size_t)c->pitch * c->esize, f, w, w,
+                          (size_t)16 * c->cfg.ny,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          c->stream));
+  return reset_status(c, (unsigned long long)step);
+}
+
+int lbm_element_size(lbm_ctx* c) { return c ? c->esize : 0; }
+
+const char* lbm_last_error(lbm_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

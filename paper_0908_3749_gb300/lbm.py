@@ -1,0 +1,219 @@
+"""ctypes binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the scheme: all of that runs in the CUDA kernels of
+``_build/liblbm.so``. Errors come back as ``LBMError`` carrying the status code
+and ``lbm_last_error``. There is no CPU fallback: if the library cannot be
+built or loaded, ``load()`` raises.
+
+Arrays: numpy float64 arrays are host buffers; torch CUDA tensors are device
+buffers (their ``data_ptr()`` is passed with on_device = 1). Field arrays are
+[ny][nx], C-contiguous, float64.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+LBM_OK = 0
+LBM_ERR_INVALID = -1
+LBM_ERR_UNSUPPORTED = -2
+LBM_ERR_CUDA = -3
+LBM_ERR_OOM = -4
+LBM_ERR_NONFINITE = -5
+LBM_ERR_TIMEOUT = -6
+
+LBM_FP64, LBM_FP32, LBM_TC_BF16X3, LBM_TC_TF32X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "tc_bf16x3": LBM_TC_BF16X3,
+              "tc_tf32x3": LBM_TC_TF32X3}
+BC = {"periodic": 0, "eq": 1, "reflect": 2, "extrap": 3, "wall": 4}
+AUDIT_RING = 1024
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lbm status %d: %s" % (code, msg))
+        self.code = code
+
+
+class lbm_bc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("rho", ctypes.c_double), ("u", ctypes.c_double),
+                ("v", ctypes.c_double), ("T", ctypes.c_double)]
+
+
+class lbm_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dt", ctypes.c_double),
+                ("s", ctypes.c_double * 16), ("internal_dof", ctypes.c_int),
+                ("precision", ctypes.c_int), ("bc", lbm_bc * 4),
+                ("audit_every", ctypes.c_int)]
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_ll = ctypes.c_longlong
+_SIGS = {
+    "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_config), _vp, ctypes.POINTER(_vp)]),
+    "lbm_set_init": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lbm_step": (ctypes.c_int, [_vp, _ll]),
+    "lbm_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lbm_destroy": (ctypes.c_int, [_vp]),
+    "lbm_audit": (ctypes.c_int, [_vp, _vp]),
+    "lbm_audit_log": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_status": (ctypes.c_int, [_vp, ctypes.POINTER(_ll), ctypes.POINTER(_ll)]),
+    "lbm_step_count": (_ll, [_vp]),
+    "lbm_get_populations": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_ll), ctypes.c_int]),
+    "lbm_set_populations": (ctypes.c_int, [_vp, _vp, _ll, ctypes.c_int]),
+    "lbm_element_size": (ctypes.c_int, [_vp]),
+    "lbm_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Loads liblbm.so (building it with nvcc first if it is missing or
+    stale). Raises if it cannot be built or loaded."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("liblbm.so is not built (%s)" % _build.LIB)
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _err(ctx=None):
+    return load().lbm_last_error(ctx).decode()
+
+
+def _check(rc, ctx=None):
+    if rc != LBM_OK:
+        raise LBMError(rc, _err(ctx))
+    return rc
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data, 0
+
+
+def make_config(nx, ny, dx, dy, dt, s, bc, precision="fp64", audit_every=0,
+                internal_dof=0):
+    """lbm_config from plain values; ``bc`` is four (kind, state) pairs for
+    x-, x+, y-, y+ with kind a name in ``BC`` and state (rho, u, v, T) or None."""
+    c = lbm_config()
+    c.nx, c.ny = int(nx), int(ny)
+    c.dx, c.dy, c.dt = float(dx), float(dy), float(dt)
+    for k in range(16):
+        c.s[k] = float(s[k])
+    c.internal_dof = int(internal_dof)
+    c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    for k, (kind, state) in enumerate(bc):
+        c.bc[k].kind = BC[kind] if isinstance(kind, str) else int(kind)
+        if state is not None:
+            c.bc[k].rho, c.bc[k].u, c.bc[k].v, c.bc[k].T = (float(x) for x in state)
+    c.audit_every = int(audit_every)
+    return c
+
+
+def lbm_create(cfg, stream=None):
+    """Returns the context handle (int). ``stream``: a cudaStream_t as int,
+    a torch.cuda.Stream, or None."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = _vp()
+    _check(load().lbm_create(ctypes.byref(cfg), _vp(stream or None), ctypes.byref(out)))
+    return out.value
+
+
+def lbm_set_init(ctx, rho, u, v, T):
+    ps = [_ptr(a) for a in (rho, u, v, T)]
+    dev = {d for _, d in ps}
+    if len(dev) != 1:
+        raise ValueError("fields must all be host arrays or all device tensors")
+    _check(load().lbm_set_init(ctx, *[p for p, _ in ps], dev.pop()), ctx)
+
+
+def lbm_step(ctx, nsteps):
+    _check(load().lbm_step(ctx, int(nsteps)), ctx)
+
+
+def lbm_moments(ctx, rho=None, u=None, v=None, T=None):
+    ps = [_ptr(a) for a in (rho, u, v, T)]
+    dev = {d for p, d in ps if p is not None}
+    if len(dev) > 1:
+        raise ValueError("outputs must all be host arrays or all device tensors")
+    _check(load().lbm_moments(ctx, *[p for p, _ in ps], dev.pop() if dev else 0), ctx)
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        _check(load().lbm_destroy(ctx))
+
+
+def lbm_audit(ctx):
+    buf = (ctypes.c_double * 4)()
+    _check(load().lbm_audit(ctx, ctypes.cast(buf, _vp)), ctx)
+    return list(buf)
+
+
+def lbm_audit_log(ctx, max_entries=AUDIT_RING):
+    tot = (ctypes.c_double * (4 * max_entries))()
+    st = (ctypes.c_longlong * max_entries)()
+    n = ctypes.c_int()
+    _check(load().lbm_audit_log(ctx, ctypes.cast(tot, _vp), ctypes.cast(st, _vp),
+                                int(max_entries), ctypes.byref(n)), ctx)
+    k = n.value
+    return [list(tot[4 * i:4 * i + 4]) for i in range(k)], list(st[:k])
+
+
+def lbm_status(ctx):
+    """(rc, first_bad_step, first_negT_step); rc is LBM_OK or
+    LBM_ERR_NONFINITE (not raised), other codes raise."""
+    a, b = _ll(), _ll()
+    rc = load().lbm_status(ctx, ctypes.byref(a), ctypes.byref(b))
+    if rc not in (LBM_OK, LBM_ERR_NONFINITE):
+        _check(rc, ctx)
+    return rc, a.value, b.value
+
+
+def lbm_step_count(ctx):
+    return int(load().lbm_step_count(ctx))
+
+
+def lbm_get_populations(ctx, out):
+    p, dev = _ptr(out)
+    step = _ll()
+    _check(load().lbm_get_populations(ctx, p, ctypes.byref(step), dev), ctx)
+    return step.value
+
+
+def lbm_set_populations(ctx, f, step):
+    p, dev = _ptr(f)
+    _check(load().lbm_set_populations(ctx, p, int(step), dev), ctx)
+
+
+def lbm_element_size(ctx):
+    return int(load().lbm_element_size(ctx))
+
+
+def lbm_last_error(ctx=None):
+    return _err(ctx)

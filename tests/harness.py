@@ -1,0 +1,78 @@
+"""Shared helpers of the tests: run a workload on the GPU through the C ABI and
+on the oracle, and compare fields the way the parity bar defines it.
+
+Relative L-infinity per field: max |a - b| / max |b| for rho; the two
+velocity components share the maximum speed of the reference as denominator
+(a pointwise relative error is meaningless where u = 0); T is recovered as
+e/rho - |u|^2/2, a difference of two terms, so its error is taken relative to
+the larger of them, max(e/rho) = max(T + |u|^2/2) of the reference;
+populations use the largest reference population.
+
+FP64 tolerance: 1e-12 for runs of up to 100 steps, 1e-14 per step beyond:
+the oracle's own FP64 rounding, measured against an extended-precision run of
+the same algorithm, grows about linearly with the step count at roughly this
+rate (tests/test_oracle_rounding.py), so no FP64 evaluation in a different
+operation order can stay within a fixed 1e-12 over thousands of steps.
+"""
+import numpy as np
+
+import workloads as W
+
+
+def gpu_run(w, nsteps, precision="fp64", audit_every=0, chunks=None, stream=None):
+    """Runs ``nsteps`` steps of workload ``w`` through the C ABI. Returns
+    (fields dict, populations (16, ny, nx) float64, status tuple, ctx-free)."""
+    from paper_0908_3749_gb300 import lbm
+    cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, precision, audit_every)
+    ctx = lbm.lbm_create(cfg, stream)
+    try:
+        lbm.lbm_set_init(ctx, *[np.ascontiguousarray(a, dtype=np.float64) for a in w.fields()])
+        for n in (chunks or [nsteps]):
+            lbm.lbm_step(ctx, n)
+        out = {k: np.empty((w.ny, w.nx)) for k in ("rho", "u", "v", "T")}
+        lbm.lbm_moments(ctx, out["rho"], out["u"], out["v"], out["T"])
+        es = lbm.lbm_element_size(ctx)
+        f = np.empty((16, w.ny, w.nx), dtype=np.float64 if es == 8 else np.float32)
+        lbm.lbm_get_populations(ctx, f)
+        status = lbm.lbm_status(ctx)
+    finally:
+        lbm.lbm_destroy(ctx)
+    return out, f.astype(np.float64), status
+
+
+def oracle_run(w, nsteps):
+    from oracle import scheme
+    f = scheme.init_populations(*w.fields())
+    f, _ = scheme.run(f, w.cfg(), nsteps)
+    rho, u, v, T = scheme.macroscopic(f)
+    return {"rho": rho, "u": u, "v": v, "T": T}, f
+
+
+def field_errors(got, ref):
+    speed2 = ref["u"] ** 2 + ref["v"] ** 2
+    speed = np.sqrt(speed2).max()
+    speed = speed if speed > 0 else 1.0
+    escale = np.abs(ref["T"] + 0.5 * speed2).max()
+    return {
+        "rho": float(np.abs(got["rho"] - ref["rho"]).max() / np.abs(ref["rho"]).max()),
+        "u": float(np.abs(got["u"] - ref["u"]).max() / speed),
+        "v": float(np.abs(got["v"] - ref["v"]).max() / speed),
+        "T": float(np.abs(got["T"] - ref["T"]).max() / escale),
+    }
+
+
+def fp64_tol(nsteps):
+    return max(1e-12, 1e-14 * nsteps)
+
+
+def l1_errors(got, ref):
+    """Sec. V.A's E = sum |num - exa| / sum |exa| per field."""
+    return {k: float(np.abs(got[k] - ref[k]).sum() / max(np.abs(ref[k]).sum(), 1e-300))
+            for k in ("rho", "u", "v", "T")}
+
+
+def pop_error(f, fref):
+    return float(np.abs(f - fref).max() / np.abs(fref).max())
+
+
+__all__ = ["gpu_run", "oracle_run", "field_errors", "pop_error", "fp64_tol", "l1_errors", "W"]

@@ -1,0 +1,57 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point the
+headers in include/ declare, and rejects invalid configurations on the host
+before touching a GPU."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*[\s\*]+(lbm\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_0908_3749_gb300 import lbm
+    lib = lbm.load()
+    names = _declared()
+    assert {"lbm_create", "lbm_set_init", "lbm_step", "lbm_moments", "lbm_destroy"} <= names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("change,code", [
+    ({"nx": 0}, -1), ({"ny": 0}, -1), ({"dt": 0.0}, -1), ({"dx": -1.0}, -1),
+    ({"dt": 1.0}, -1),                         # Courant number 6 dt/dx > 1
+    ({"internal_dof": 3}, -2), ({"precision": 7}, -2),
+    ({"s0": float("nan")}, -1), ({"bc0": ("periodic", None)}, -1),   # periodic on one side only
+    ({"audit_every": -1}, -1),
+])
+def test_create_rejects_bad_configs_on_host(change, code):
+    from paper_0908_3749_gb300 import lbm
+    kw = dict(nx=8, ny=4, dx=0.01, dy=0.01, dt=1e-5, s=[1e5] * 16,
+              bc=[("eq", (1, 0, 0, 1)), ("eq", (1, 0, 0, 1)), ("periodic", None), ("periodic", None)],
+              precision="fp64", audit_every=0, internal_dof=0)
+    for k, v in change.items():
+        if k == "s0":
+            kw["s"] = [v] + kw["s"][1:]
+        elif k == "bc0":
+            kw["bc"] = [v] + kw["bc"][1:]
+        else:
+            kw[k] = v
+    cfg = lbm.make_config(**kw)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_create(cfg)
+    assert ei.value.code == code
+    assert lbm.lbm_last_error(None)
