@@ -212,6 +212,48 @@ def e2e_steps(torch, lbm, ctx, w, K, W):
     return times, f.numel() * 4, sum(o.numel() * 8 for o in outs)
 
 
+def tubes_measure(torch, lbm, stream, args):
+    """4096 seeded quasi-1D Riemann problems (Nx ~ U[128, 2048]) in one
+    persistent launch per call: the autotuned tiling, then timed calls of
+    ``--tube-steps`` steps each (inputs larger than L2)."""
+    import workloads
+    B = workloads.tube_batch()
+    nt = len(B["nx"])
+    b = lbm.lbm_batch_create(B["nx"], B["dx"], B["dt"], B["s"], B["left"], B["right"], stream)
+    try:
+        fields = []
+        for q in range(4):
+            parts = []
+            for t in range(nt):
+                x = (np.arange(B["nx"][t]) + 0.5) / B["nx"][t]
+                parts.append(np.where(x <= 0.5, B["left"][t, q], B["right"][t, q]))
+            fields.append(np.concatenate(parts))
+        lbm.lbm_batch_set_init(b, *fields)
+        chosen = lbm.lbm_batch_autotune(b, 20, None)
+        n = args.tube_steps
+        lbm.lbm_batch_step(b, n)               # capture + warm-up
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        times = []
+        with torch.cuda.stream(stream):
+            for k in range(3):
+                ev[0].record(stream)
+                lbm.lbm_batch_step(b, n)
+                ev[1].record(stream)
+                stream.synchronize()
+                times.append(ev[0].elapsed_time(ev[1]))
+        rc, bad, nbad, to = lbm.lbm_batch_status(b, nt)
+        total = lbm.lbm_batch_total_nodes(b)
+        ms = min(times) / n
+        return {"workload": "4096_tubes_nx_128_2048", "nodes": total, "steps_per_launch": n,
+                "value": total / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                "achieved_gbs": BYTES_PER_CELL["fp32"] * total / (ms * 1e-3) / 1e9,
+                "tiling": list(chosen), "unstable_tubes": nbad, "timeout": to,
+                "graph": True, "launches_per_call": 1}
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -273,8 +315,8 @@ def run_ours(args):
     # set-up, 268 MB of traffic per step): the HBM-bound regime.
     large = None
     if not args.no_large:
-        import workloads as W
-        wl = W.shock_bubble()
+        import workloads
+        wl = workloads.shock_bubble()
         ctxl = make_ctx(lbm, wl, "fp32", args.audit_every, stream)
         tl = time_steps(torch, lbm, ctxl, stream, flush, min(K, 50), W)
         lbm.lbm_destroy(ctxl)
@@ -283,6 +325,8 @@ def run_ours(args):
         gbl = BYTES_PER_CELL["fp32"] * cl / (msl * 1e-3) / 1e9
         large = {"workload": "shock_bubble_%dx%d" % (wl.nx, wl.ny), "value": cl / (msl * 1e-3),
                  "unit": UNIT, "ms_per_step": msl, "achieved_gbs": gbl, "steps": len(tl)}
+
+    tubes = None if args.no_tubes else tubes_measure(torch, lbm, stream, args)
 
     if rank != 0:
         if dist:
@@ -299,6 +343,8 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     if large:
         large["frac_of_hbm"] = large["achieved_gbs"] / hbm_peak
+    if tubes:
+        tubes["frac_of_hbm"] = tubes["achieved_gbs"] / hbm_peak
     tflops64 = FLOPS_PER_CELL * cells / (ms64 * 1e-3) / 1e12
     line = {
         "metric": METRIC,
@@ -330,6 +376,7 @@ def run_ours(args):
                               "hbm_frac": BYTES_PER_CELL["fp64"] * cells / (ms64 * 1e-3) / 1e9 / hbm_peak}},
         "status": {"fp32": list(s32), "fp64": list(s64)},
         "fp32_large_grid": large,
+        "tubes": tubes,
         "e2e": {"value": cells / statistics.mean(e2e_t), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "lbm_set_populations(pinned host) + lbm_step(1) + lbm_moments(pinned host)"},
@@ -375,6 +422,8 @@ def main():
     ap.add_argument("--audit-every", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-tubes", action="store_true")
+    ap.add_argument("--tube-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()

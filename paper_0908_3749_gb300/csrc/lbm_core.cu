@@ -40,8 +40,8 @@ constexpr unsigned long long NONE = ~0ull;
 // Thread-block shapes: FP32 32 x 8 (memory-bound, more warps in flight),
 // FP64 32 x 4 (FP64-ALU-bound; smaller blocks balance the SMs better).
 template <typename R> struct Shape;
-template <> struct Shape<float> { static constexpr int X = 32, Y = 8; };
-template <> struct Shape<double> { static constexpr int X = 32, Y = 4; };
+template <> struct Shape<float> { static constexpr int X = 32, Y = 8, MINB = 4; };
+template <> struct Shape<double> { static constexpr int X = 32, Y = 4, MINB = 4; };
 constexpr int AUX_X = 32, AUX_Y = 8, AUX_N = AUX_X * AUX_Y;  // init / moments / audit
 
 // Device-resident status block of one context.
@@ -185,7 +185,7 @@ __device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict_
 // Off: unsigned (32-bit element offsets, grids with 16 * plane < 2^32) or
 // long long. One thread per node.
 template <typename R, typename Off>
-__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y)
+__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
     k_step(const R* __restrict__ fin, R* __restrict__ fout, const StepArgs<R> A) {
   constexpr int BXD = Shape<R>::X, BYD = Shape<R>::Y, N = BXD * BYD;
   __shared__ double sm[N / 4][4];

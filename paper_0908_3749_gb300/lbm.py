@@ -217,3 +217,141 @@ def lbm_element_size(ctx):
 
 def lbm_last_error(ctx=None):
     return _err(ctx)
+
+
+# ----------------------------------------------------------------------------
+# Batches of quasi-1D tubes (include/lbm_batch.h)
+# ----------------------------------------------------------------------------
+class lbm_batch_config(ctypes.Structure):
+    _fields_ = [("ntubes", ctypes.c_int), ("nx", ctypes.POINTER(ctypes.c_int)),
+                ("dx", ctypes.POINTER(ctypes.c_double)), ("dt", ctypes.c_double),
+                ("s", ctypes.POINTER(ctypes.c_double)), ("left", ctypes.POINTER(ctypes.c_double)),
+                ("right", ctypes.POINTER(ctypes.c_double))]
+
+
+_BATCH_SIGS = {
+    "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(lbm_batch_config), _vp, ctypes.POINTER(_vp)]),
+    "lbm_batch_set_init": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lbm_batch_step": (ctypes.c_int, [_vp, _ll]),
+    "lbm_batch_moments": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]),
+    "lbm_batch_audit": (ctypes.c_int, [_vp, _vp]),
+    "lbm_batch_status": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_set_tiling": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_get_tiling": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_debug_skip_arrival": (ctypes.c_int, [_vp, ctypes.c_int, _ll]),
+    "lbm_batch_step_count": (_ll, [_vp]),
+    "lbm_batch_total_nodes": (ctypes.c_int, [_vp, ctypes.POINTER(_ll)]),
+    "lbm_batch_destroy": (ctypes.c_int, [_vp]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
+}
+_SIGS.update(_BATCH_SIGS)
+_KEEP = {}
+
+
+def _bcheck(rc, b=None):
+    if rc != LBM_OK:
+        raise LBMError(rc, load().lbm_batch_last_error(b).decode())
+    return rc
+
+
+def lbm_batch_create(nx, dx, dt, s, left, right, stream=None):
+    """nx: ints per tube; dx: spacing per tube; s: [ntubes][16]; left/right:
+    [ntubes][4] (rho, u, v, T). Returns the batch handle."""
+    import numpy as np
+    nx = np.ascontiguousarray(nx, dtype=np.int32)
+    dx = np.ascontiguousarray(dx, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    left = np.ascontiguousarray(left, dtype=np.float64)
+    right = np.ascontiguousarray(right, dtype=np.float64)
+    cfg = lbm_batch_config()
+    cfg.ntubes = len(nx)
+    cfg.nx = nx.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    cfg.dx = dx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    cfg.dt = float(dt)
+    cfg.s = s.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    cfg.left = left.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    cfg.right = right.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = _vp()
+    _bcheck(load().lbm_batch_create(ctypes.byref(cfg), _vp(stream or None), ctypes.byref(out)))
+    return out.value
+
+
+def lbm_batch_set_init(b, rho, u, v, T):
+    ps = [_ptr(a) for a in (rho, u, v, T)]
+    dev = {d for _, d in ps}
+    if len(dev) != 1:
+        raise ValueError("fields must all be host arrays or all device tensors")
+    _bcheck(load().lbm_batch_set_init(b, *[p for p, _ in ps], dev.pop()), b)
+
+
+def lbm_batch_step(b, nsteps):
+    _bcheck(load().lbm_batch_step(b, int(nsteps)), b)
+
+
+def lbm_batch_moments(b, rho=None, u=None, v=None, T=None):
+    ps = [_ptr(a) for a in (rho, u, v, T)]
+    dev = {d for p, d in ps if p is not None}
+    _bcheck(load().lbm_batch_moments(b, *[p for p, _ in ps], dev.pop() if dev else 0), b)
+
+
+def lbm_batch_audit(b, ntubes):
+    import numpy as np
+    out = np.empty((ntubes, 4))
+    _bcheck(load().lbm_batch_audit(b, out.ctypes.data), b)
+    return out
+
+
+def lbm_batch_status(b, ntubes):
+    """(rc, first_bad[ntubes] (-1 = fine), nbad, timeout); LBM_ERR_TIMEOUT is
+    returned in rc, not raised."""
+    import numpy as np
+    fb = np.empty(ntubes, dtype=np.int64)
+    nbad, to = ctypes.c_int(), ctypes.c_int()
+    rc = load().lbm_batch_status(b, fb.ctypes.data, ctypes.byref(nbad), ctypes.byref(to))
+    if rc not in (LBM_OK, LBM_ERR_TIMEOUT):
+        _bcheck(rc, b)
+    return rc, fb, nbad.value, to.value
+
+
+def lbm_batch_set_tiling(b, tile, threads):
+    _bcheck(load().lbm_batch_set_tiling(b, int(tile), int(threads)), b)
+
+
+def lbm_batch_get_tiling(b):
+    t, th, bl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(load().lbm_batch_get_tiling(b, ctypes.byref(t), ctypes.byref(th), ctypes.byref(bl)), b)
+    return t.value, th.value, bl.value
+
+
+def lbm_batch_autotune(b, trial_steps=20, cache_path=None):
+    chosen = (ctypes.c_int * 2)()
+    path = cache_path.encode() if cache_path else None
+    _bcheck(load().lbm_batch_autotune(b, int(trial_steps), path, chosen), b)
+    return chosen[0], chosen[1]
+
+
+def lbm_batch_debug_skip_arrival(b, block, step):
+    _bcheck(load().lbm_batch_debug_skip_arrival(b, int(block), int(step)), b)
+
+
+def lbm_batch_step_count(b):
+    return int(load().lbm_batch_step_count(b))
+
+
+def lbm_batch_total_nodes(b):
+    n = _ll()
+    _bcheck(load().lbm_batch_total_nodes(b, ctypes.byref(n)), b)
+    return n.value
+
+
+def lbm_batch_destroy(b):
+    if b:
+        _bcheck(load().lbm_batch_destroy(b))
+
+
+def lbm_batch_last_error(b=None):
+    return load().lbm_batch_last_error(b).decode()
