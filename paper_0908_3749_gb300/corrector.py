@@ -1,0 +1,142 @@
+"""Learned coarse-grid corrector: data generation, training and evaluation.
+
+Orchestration only: every field, restriction, forward and backward pass and
+optimiser update runs in the CUDA kernels behind ``include/lbm.h`` and
+``include/lbm_cnn.h``; this module moves device pointers between them.
+
+Data: for each seeded problem (a callable ``make(seed, n, dt)`` returning a
+workload with ``nx, ny, dx, dy, dt, s, bc`` and initial fields), a fine run
+on an (r n) x (r n) grid with dt / r and a coarse run on n x n with dt, both
+to the same end time, through the FP32 step. The fine result restricted by r
+(block means of rho, j, e) is the target of the coarse result. Problems whose
+fine or coarse run trips the watchdog are skipped and counted.
+"""
+import math
+import time
+
+import numpy as np
+
+from . import lbm
+
+
+def run_fields(w, nsteps, precision="fp32", stream=None):
+    """Runs workload ``w`` for ``nsteps`` and returns (fields, ok): fields a
+    CUDA float64 tensor [4][ny][nx] (rho, u, v, T); ok is False when the
+    watchdog tripped or the final state is not finite with rho > 0 and
+    T > 0 everywhere (the network takes log rho and log T)."""
+    import torch
+    cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, precision, 0)
+    ctx = lbm.lbm_create(cfg, stream)
+    try:
+        dev = [torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in
+               (w.rho, w.u, w.v, w.T)]
+        lbm.lbm_set_init(ctx, *dev)
+        lbm.lbm_step(ctx, nsteps)
+        out = torch.empty((4, w.ny, w.nx), dtype=torch.float64, device="cuda")
+        lbm.lbm_moments(ctx, out[0], out[1], out[2], out[3])
+        rc, bad, _ = lbm.lbm_status(ctx)
+    finally:
+        lbm.lbm_destroy(ctx)
+    ok = (rc == lbm.LBM_OK and bad < 0 and bool(torch.isfinite(out).all())
+          and bool((out[0] > 0).all()) and bool((out[3] > 0).all()))
+    return out, ok
+
+
+def make_pairs(make, seeds, n, ratio, t_end, dt=1e-5, stream=None):
+    """(pairs, skipped, timing): pairs of (coarse, target) CUDA tensors."""
+    import torch
+    pairs, skipped = [], 0
+    t_fine = t_coarse = 0.0
+    nc = int(round(t_end / dt))
+    nf = nc * ratio
+    for seed in seeds:
+        wf = make(seed, n * ratio, dt / ratio)
+        wc = make(seed, n, dt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fine, ok_f = run_fields(wf, nf, stream=stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        coarse, ok_c = run_fields(wc, nc, stream=stream)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        t_fine += t1 - t0
+        t_coarse += t2 - t1
+        if not (ok_f and ok_c):
+            skipped += 1
+            continue
+        target = torch.empty((4, n, n), dtype=torch.float64, device="cuda")
+        lbm.lbm_restrict(fine, ratio, target)
+        if not (bool((target[3] > 0).all()) and bool(torch.isfinite(target).all())):
+            skipped += 1
+            continue
+        pairs.append((coarse, target))
+    torch.cuda.synchronize()
+    used = max(len(seeds), 1)
+    return pairs, skipped, {"fine_s_per_problem": t_fine / used,
+                            "coarse_s_per_problem": t_coarse / used}
+
+
+def init_params(seed):
+    """He-normal weights (biases zero) from a seeded generator; the last
+    layer starts at zero so the untrained corrector is the identity."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    ch = lbm.CNN_CHANNELS
+    for l in range(len(ch) - 1):
+        cin, cout = ch[l], ch[l + 1]
+        if l == len(ch) - 2:
+            w = np.zeros((3, 3, cin, cout))
+        else:
+            w = rng.standard_normal((3, 3, cin, cout)) * math.sqrt(2.0 / (9 * cin))
+        parts += [w.reshape(-1), np.zeros(cout)]
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == lbm.CNN_NPARAMS
+    return p
+
+
+def train(pairs, epochs=20, lr=1e-3, seed=0, stream=None, log_every=0):
+    """Trains a fresh network on ``pairs``; returns (handle, losses).
+    The caller owns the handle (lbm.lbm_cnn_destroy)."""
+    H, W = pairs[0][0].shape[1:]
+    net = lbm.lbm_cnn_create(H, W, stream)
+    lbm.lbm_cnn_set_params(net, init_params(seed))
+    lbm.lbm_cnn_set_adam(net, lr)
+    rng = np.random.default_rng(seed + 1)
+    losses = []
+    for ep in range(epochs):
+        tot = 0.0
+        for k in rng.permutation(len(pairs)):
+            tot += lbm.lbm_cnn_train_step(net, pairs[k][0], pairs[k][1])
+        losses.append(tot / len(pairs))
+        if not math.isfinite(losses[-1]):
+            raise FloatingPointError("training loss is not finite at epoch %d" % ep)
+        if log_every and ep % log_every == 0:
+            print("epoch %d loss %.4g" % (ep, losses[-1]))
+    return net, losses
+
+
+def rel_l1(a, b):
+    """Sec. V.A's E per field: sum |a - b| / sum |b| over the grid."""
+    return [float((a[k] - b[k]).abs().sum() / b[k].abs().sum()) for k in range(4)]
+
+
+def evaluate(net, pairs, mass_tol=1e-2):
+    """Mean relative L1 error per field (rho, u, v, T) of the plain coarse
+    fields and of the corrected ones against the restricted fine fields, the
+    number of fallbacks, and the inference time per problem."""
+    import torch
+    plain, corr, fallbacks, t_inf = [], [], 0, 0.0
+    for coarse, target in pairs:
+        out = torch.empty_like(coarse)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fb = lbm.lbm_cnn_correct(net, coarse, out, mass_tol)
+        torch.cuda.synchronize()
+        t_inf += time.perf_counter() - t0
+        fallbacks += int(fb)
+        plain.append(rel_l1(coarse, target))
+        corr.append(rel_l1(out, target))
+    n = max(len(pairs), 1)
+    return {"plain": np.mean(plain, axis=0).tolist(), "corrected": np.mean(corr, axis=0).tolist(),
+            "fallbacks": fallbacks, "inference_s_per_problem": t_inf / n}

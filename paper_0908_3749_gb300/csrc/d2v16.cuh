@@ -102,6 +102,11 @@ __host__ __device__ constexpr bool has_y(int i) { return !((i < 8) && !(i & 1));
 //         f+ = a0 f + aE f(x+dx) + aW f(x-dx) + aN f(y+dy) + aS f(y-dy) + df.
 template <typename R>
 struct Coeffs {
+  R F0[4][4];  // forward blocks (b0, bx, by, bc2, bs2 in the type R)
+  R FX[4][4];
+  R FY[4][4];
+  R FC[2][2];
+  R FS[2][2];
   R E0[4][4];  // rows S'_g; columns rho, e, m11, m12
   R EX[4][4];  // rows X'_g; columns j_x, m7, m9, m15
   R EY[4][4];  // rows Y'_g; columns j_y, m8, m10, m16
@@ -114,6 +119,22 @@ struct Coeffs {
   R KS[2][2];  // w-scaled ES
   R a0[16], aE[16], aW[16], aN[16], aS[16];
 };
+
+// Fills the forward blocks of K from the coefficient tables above.
+template <typename R>
+inline void fill_forward(Coeffs<R>& K) {
+  for (int r = 0; r < 4; ++r)
+    for (int g = 0; g < 4; ++g) {
+      K.F0[r][g] = (R)b0(r, g);
+      K.FX[r][g] = (R)bx(r, g);
+      K.FY[r][g] = (R)by(r, g);
+    }
+  for (int r = 0; r < 2; ++r)
+    for (int g = 0; g < 2; ++g) {
+      K.FC[r][g] = (R)bc2(r, g);
+      K.FS[r][g] = (R)bs2(r, g);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Device arithmetic
@@ -158,18 +179,6 @@ __device__ __forceinline__ void transform(const R f[16], Groups<R>& d) {
       d.Y[g] = a + b;
     }
   }
-}
-
-// Table selectors (types, so that every coefficient is a compile-time constant).
-struct TabS { __host__ __device__ static constexpr double at(int r, int g) { return b0(r, g); } };
-struct TabX { __host__ __device__ static constexpr double at(int r, int g) { return bx(r, g); } };
-struct TabY { __host__ __device__ static constexpr double at(int r, int g) { return by(r, g); } };
-
-// Row r of a 4 x 4 block table applied to a group vector.
-template <typename Tab, typename R>
-__device__ __forceinline__ R dot4(int r, const R (&v)[4]) {
-  return R(Tab::at(r, 0)) * v[0] + R(Tab::at(r, 1)) * v[1] +
-         R(Tab::at(r, 2)) * v[2] + R(Tab::at(r, 3)) * v[3];
 }
 
 // Inverse 4-point transform from scaled group values to populations.
@@ -249,13 +258,19 @@ struct Cons {
   R rho, jx, jy, e;
 };
 
+// Row r of a forward block (given in the arithmetic type) times a group vector.
 template <typename R>
-__device__ __forceinline__ Cons<R> conserved(const Groups<R>& d) {
+__device__ __forceinline__ R row4(const R (&b)[4][4], int r, const R (&v)[4]) {
+  return b[r][0] * v[0] + b[r][1] * v[1] + b[r][2] * v[2] + b[r][3] * v[3];
+}
+
+template <typename R>
+__device__ __forceinline__ Cons<R> conserved(const Coeffs<R>& K, const Groups<R>& d) {
   Cons<R> c;
   c.rho = (d.S[0] + d.S[1]) + (d.S[2] + d.S[3]);
-  c.e = dot4<TabS>(1, d.S);
-  c.jx = dot4<TabX>(0, d.X);
-  c.jy = dot4<TabY>(0, d.Y);
+  c.e = row4(K.F0, 1, d.S);
+  c.jx = row4(K.FX, 0, d.X);
+  c.jy = row4(K.FY, 0, d.Y);
   return c;
 }
 
@@ -265,18 +280,18 @@ template <typename R>
 __device__ __forceinline__ R collide(const Coeffs<R>& K, const Groups<R>& d,
                                      const Cons<R>& c, R df[16]) {
   const Eq<R> q = equilibria(c.rho, c.jx, c.jy, c.e);
-  const R d11 = dot4<TabS>(2, d.S) - q.m11;
-  const R d12 = dot4<TabS>(3, d.S);                // m12^eq = 0
-  const R d7 = dot4<TabX>(1, d.X) - q.m7;
-  const R d9 = dot4<TabX>(2, d.X) - q.m9;
-  const R d15 = dot4<TabX>(3, d.X);                // m15^eq = 0
-  const R d8 = dot4<TabY>(1, d.Y) - q.m8;
-  const R d10 = dot4<TabY>(2, d.Y) - q.m10;
-  const R d16 = dot4<TabY>(3, d.Y);                // m16^eq = 0
-  const R d5 = R(bc2(0, 0)) * d.C[0] + R(bc2(0, 1)) * d.C[1] - q.m5;
-  const R d13 = R(bc2(1, 0)) * d.C[0] + R(bc2(1, 1)) * d.C[1] - q.m13;
-  const R d6 = R(bs2(0, 0)) * d.C[2] + R(bs2(0, 1)) * d.C[3] - q.m6;
-  const R d14 = R(bs2(1, 0)) * d.C[2] + R(bs2(1, 1)) * d.C[3] - q.m14;
+  const R d11 = row4(K.F0, 2, d.S) - q.m11;
+  const R d12 = row4(K.F0, 3, d.S);                // m12^eq = 0
+  const R d7 = row4(K.FX, 1, d.X) - q.m7;
+  const R d9 = row4(K.FX, 2, d.X) - q.m9;
+  const R d15 = row4(K.FX, 3, d.X);                // m15^eq = 0
+  const R d8 = row4(K.FY, 1, d.Y) - q.m8;
+  const R d10 = row4(K.FY, 2, d.Y) - q.m10;
+  const R d16 = row4(K.FY, 3, d.Y);                // m16^eq = 0
+  const R d5 = K.FC[0][0] * d.C[0] + K.FC[0][1] * d.C[1] - q.m5;
+  const R d13 = K.FC[1][0] * d.C[0] + K.FC[1][1] * d.C[1] - q.m13;
+  const R d6 = K.FS[0][0] * d.C[2] + K.FS[0][1] * d.C[3] - q.m6;
+  const R d14 = K.FS[1][0] * d.C[2] + K.FS[1][1] * d.C[3] - q.m14;
   R S[4], C[4], X[4], Y[4];
 #pragma unroll
   for (int g = 0; g < 4; ++g) {

@@ -1,0 +1,611 @@
+// lbm_cnn.cu -- training and inference kernels of the coarse-grid corrector
+// (include/lbm_cnn.h).
+//
+// Activations are BF16, pixel-major (NHWC, one image): a[p][c], p = y W + x.
+// 3 x 3 convolutions are implicit GEMMs on the tensor cores
+// (mma.sync m16n8k16, BF16 inputs, FP32 accumulation): rows are pixels, the
+// reduction index k = tap * CIN + ci runs over the 9 taps and the input
+// channels, columns are output channels. The weights of a layer are packed
+// once per update into [COUT][K] BF16 (K contiguous, the "col" operand) for
+// the forward pass and into the tap-flipped, channel-transposed [CIN][K'] for
+// the input-gradient pass, which is the same GEMM run on the output
+// gradients. Weight gradients are FP32 sums over pixels on the CUDA cores
+// (per-block partials, then a fixed-order sum: reproducible). Adam keeps FP32
+// master weights.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm_cnn.h"
+
+namespace {
+
+constexpr int NL = LBM_CNN_LAYERS;
+constexpr int CH[NL + 1] = {4, 32, 32, 32, 32, 4};
+__host__ __device__ constexpr int ru(int a, int m) { return (a + m - 1) / m * m; }
+
+__host__ __device__ constexpr int wsize(int l) { return 9 * (l == 0 ? 4 : 32) * (l == NL - 1 ? 4 : 32); }
+__host__ __device__ constexpr int cin_of(int l) { return l == 0 ? 4 : 32; }
+__host__ __device__ constexpr int cout_of(int l) { return l == NL - 1 ? 4 : 32; }
+
+int param_offset(int l) {  // start of layer l in the packed parameter vector
+  int o = 0;
+  for (int k = 0; k < l; ++k) o += wsize(k) + cout_of(k);
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core implicit-GEMM 3 x 3 convolution
+// ---------------------------------------------------------------------------
+enum Epi { EPI_RELU_BF16 = 0, EPI_LINEAR_F32 = 1, EPI_MASK_BF16 = 2 };
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4],
+                                         unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+      "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Two consecutive channels (k, k+1) of the patch element of pixel (y, x) for
+// reduction index k (k even, CIN even so both share a tap); zero outside the
+// image or beyond the real K.
+template <int CIN>
+__device__ __forceinline__ unsigned patch2(const __nv_bfloat16* __restrict__ in, int H, int W,
+                                           bool valid, int y, int x, int k) {
+  if (!valid || k >= 9 * CIN) return 0u;
+  const int tap = k / CIN, ci = k - tap * CIN;
+  const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+  if (yy < 0 || yy >= H || xx < 0 || xx >= W) return 0u;
+  return *reinterpret_cast<const unsigned*>(in + ((long long)yy * W + xx) * CIN + ci);
+}
+
+// out[p][c] (c < COUT) = epilogue(sum_k patch(p, k) * Wt[c][k]). Each warp
+// computes 16 pixels x COUTP columns; a block of 4 warps covers 64 pixels.
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16* __restrict__ in, int H, int W,
+                                              const __nv_bfloat16* __restrict__ Wt,
+                                              const float* __restrict__ bias,
+                                              const __nv_bfloat16* __restrict__ mask,
+                                              __nv_bfloat16* __restrict__ out_bf,
+                                              float* __restrict__ out_f) {
+  constexpr int KP = ru(9 * CIN, 16), COUTP = ru(COUT, 8), NF = COUTP / 8, KS = KP / 16;
+  __shared__ __align__(16) __nv_bfloat16 sw[COUTP * KP];
+  for (int i = threadIdx.x; i < COUTP * KP / 2; i += blockDim.x)
+    reinterpret_cast<unsigned*>(sw)[i] = reinterpret_cast<const unsigned*>(Wt)[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, tig = lane & 3;
+  const int npix = H * W;
+  const int p0 = blockIdx.x * 64 + warp * 16;
+  const int pa = p0 + g, pb = p0 + g + 8;
+  const bool va = pa < npix, vb = pb < npix;
+  const int ya = va ? pa / W : 0, xa = va ? pa - ya * W : 0;
+  const int yb = vb ? pb / W : 0, xb = vb ? pb - yb * W : 0;
+  float acc[NF][4];
+#pragma unroll
+  for (int j = 0; j < NF; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+#pragma unroll 2
+  for (int ks = 0; ks < KS; ++ks) {
+    const int k0 = ks * 16 + tig * 2, k1 = k0 + 8;
+    unsigned a[4];
+    a[0] = patch2<CIN>(in, H, W, va, ya, xa, k0);
+    a[1] = patch2<CIN>(in, H, W, vb, yb, xb, k0);
+    a[2] = patch2<CIN>(in, H, W, va, ya, xa, k1);
+    a[3] = patch2<CIN>(in, H, W, vb, yb, xb, k1);
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+      const __nv_bfloat16* col = sw + (j * 8 + g) * KP;
+      const unsigned b0 = *reinterpret_cast<const unsigned*>(col + k0);
+      const unsigned b1 = *reinterpret_cast<const unsigned*>(col + k1);
+      mma_bf16(acc[j], a, b0, b1);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p = h ? pb : pa;
+      if (!(h ? vb : va)) continue;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int c = j * 8 + tig * 2 + e;
+        if (c >= COUT) continue;
+        float v = acc[j][2 * h + e];
+        if (EPI == EPI_RELU_BF16) {
+          v = fmaxf(v + bias[c], 0.f);
+          out_bf[(long long)p * COUT + c] = __float2bfloat16(v);
+        } else if (EPI == EPI_LINEAR_F32) {
+          out_f[(long long)p * COUT + c] = v + bias[c];
+        } else {
+          const float keep = __bfloat162float(mask[(long long)p * COUT + c]) > 0.f ? 1.f : 0.f;
+          out_bf[(long long)p * COUT + c] = __float2bfloat16(v * keep);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Weight and bias gradients (FP32 CUDA cores, per-block partials)
+// ---------------------------------------------------------------------------
+// Thread t < 9 CIN owns the pair (tap, ci) and all COUT outputs
+// dW[tap][ci][co] = sum_p act[p + off(tap)][ci] dz[p][co]; thread 9 CIN + co
+// (co < COUT) owns db[co] = sum_p dz[p][co]. Block b sums pixels
+// [b * chunk, (b + 1) * chunk).
+template <int CIN, int COUT>
+__global__ void k_wgrad(const __nv_bfloat16* __restrict__ act, const __nv_bfloat16* __restrict__ dz,
+                        int H, int W, int chunk, float* __restrict__ partial) {
+  const int t = threadIdx.x;
+  constexpr int NW = 9 * CIN * COUT, NOUT = NW + COUT;
+  float acc[COUT];
+#pragma unroll
+  for (int c = 0; c < COUT; ++c) acc[c] = 0.f;
+  const int npix = H * W;
+  const int pbeg = blockIdx.x * chunk, pend = min(npix, pbeg + chunk);
+  const bool wthread = t < 9 * CIN;
+  const bool bthread = t >= 9 * CIN && t < 9 * CIN + COUT;
+  const int tap = wthread ? t / CIN : 0, ci = wthread ? t % CIN : 0;
+  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  for (int p = pbeg; p < pend; ++p) {
+    const int y = p / W, x = p - y * W;
+    if (wthread) {
+      const int yy = y + dy, xx = x + dx;
+      float a = 0.f;
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+        a = __bfloat162float(act[((long long)yy * W + xx) * CIN + ci]);
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) acc[c] += a * __bfloat162float(dz[(long long)p * COUT + c]);
+    } else if (bthread) {
+      acc[0] += __bfloat162float(dz[(long long)p * COUT + (t - 9 * CIN)]);
+    }
+  }
+  float* out = partial + (long long)blockIdx.x * NOUT;
+  if (wthread) {
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) out[(tap * CIN + ci) * COUT + c] = acc[c];
+  } else if (bthread) {
+    out[NW + (t - 9 * CIN)] = acc[0];
+  }
+}
+
+// grad[i] = sum over blocks b (in order) of partial[b][i].
+__global__ void k_sum_partials(const float* __restrict__ partial, int nblocks, int n,
+                               float* __restrict__ grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int b = 0; b < nblocks; ++b) s += partial[(long long)b * n + i];
+  grad[i] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Features, loss, Adam, packing, correction, restriction
+// ---------------------------------------------------------------------------
+// Planes [4][H][W] (rho, u, v, T) -> features (log rho, u, v, log T) in FP32
+// [p][4] and BF16 [p][4].
+__global__ void k_features(const double* __restrict__ f, int npix, float* __restrict__ xf,
+                           __nv_bfloat16* __restrict__ xb) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npix) return;
+  const float q[4] = {(float)log(f[p]), (float)f[npix + p], (float)f[2 * npix + p],
+                      (float)log(f[3 * npix + p])};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (xf) xf[4 * p + c] = q[c];
+    if (xb) xb[4 * p + c] = __float2bfloat16(q[c]);
+  }
+}
+
+// out = x + z; d = out - target; dz = 2 d / N (BF16); block partial of sum d^2.
+__global__ void k_loss(const float* __restrict__ xf, const float* __restrict__ z,
+                       const float* __restrict__ tf, int n, __nv_bfloat16* __restrict__ dz,
+                       double* __restrict__ partial) {
+  __shared__ double sm[256];
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  double s = 0.0;
+  if (i < n) {
+    const float d = xf[i] + z[i] - tf[i];
+    s = (double)d * d;
+    if (dz) dz[i] = __float2bfloat16(2.f * d / (float)n);
+  }
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) sm[threadIdx.x] += sm[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+__global__ void k_sum_d(const double* __restrict__ partial, int n, double scale, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += partial[i];
+    *out = s * scale;
+  }
+}
+
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, int n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Packs layer l's FP32 w[3][3][cin][cout] into the forward operand
+// Wt[cout_p][kp] (k = tap cin + ci) and the input-gradient operand
+// Wb[cin_p][kb] (k' = tap' cout + co with tap' = 8 - tap), BF16, zero padded.
+__global__ void k_pack(const float* __restrict__ w, int cin, int cout, int kp, int coutp,
+                       int kb, int cinp, __nv_bfloat16* __restrict__ wt,
+                       __nv_bfloat16* __restrict__ wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < coutp * kp) {
+    const int c = i / kp, k = i % kp;
+    float val = 0.f;
+    if (c < cout && k < 9 * cin) {
+      const int tap = k / cin, ci = k % cin;
+      val = w[(tap * cin + ci) * cout + c];
+    }
+    wt[i] = __float2bfloat16(val);
+  }
+  if (wb && i < cinp * kb) {
+    const int ci = i / kb, k = i % kb;
+    float val = 0.f;
+    if (ci < cin && k < 9 * cout) {
+      const int tp = k / cout, co = k % cout, tap = 8 - tp;
+      val = w[(tap * cin + ci) * cout + co];
+    }
+    wb[i] = __float2bfloat16(val);
+  }
+}
+
+// corrected planes from output features x + z; block partial sums of rho.
+__global__ void k_apply(const float* __restrict__ xf, const float* __restrict__ z, int npix,
+                        double* __restrict__ out, const double* __restrict__ coarse,
+                        double* __restrict__ partial) {
+  __shared__ double sm[2][256];
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  double r = 0.0, r0 = 0.0;
+  if (p < npix) {
+    const float q0 = xf[4 * p] + z[4 * p], q1 = xf[4 * p + 1] + z[4 * p + 1];
+    const float q2 = xf[4 * p + 2] + z[4 * p + 2], q3 = xf[4 * p + 3] + z[4 * p + 3];
+    r = exp((double)q0);
+    out[p] = r;
+    out[npix + p] = q1;
+    out[2 * npix + p] = q2;
+    out[3 * npix + p] = exp((double)q3);
+    r0 = coarse[p];
+    if (!isfinite(r + q1 + q2 + q3)) r = nan("");
+  }
+  sm[0][threadIdx.x] = r;
+  sm[1][threadIdx.x] = r0;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      sm[0][threadIdx.x] += sm[0][threadIdx.x + st];
+      sm[1][threadIdx.x] += sm[1][threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = sm[0][0];
+    partial[2 * blockIdx.x + 1] = sm[1][0];
+  }
+}
+
+__global__ void k_restrict(const double* __restrict__ f, int Hf, int Wf, int r,
+                           double* __restrict__ c) {
+  const int Hc = Hf / r, Wc = Wf / r;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Hc * Wc) return;
+  const int Y = p / Wc, X = p % Wc;
+  const long long nf = (long long)Hf * Wf;
+  double R = 0, JX = 0, JY = 0, E = 0;
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < r; ++b) {
+      const long long q = (long long)(Y * r + a) * Wf + (X * r + b);
+      const double rho = f[q], u = f[nf + q], v = f[2 * nf + q], T = f[3 * nf + q];
+      R += rho;
+      JX += rho * u;
+      JY += rho * v;
+      E += rho * T + 0.5 * rho * (u * u + v * v);
+    }
+  const double inv = 1.0 / (r * r);
+  R *= inv; JX *= inv; JY *= inv; E *= inv;
+  const double U = JX / R, V = JY / R;
+  const long long nc = (long long)Hc * Wc;
+  c[p] = R;
+  c[nc + p] = U;
+  c[2 * nc + p] = V;
+  c[3 * nc + p] = E / R - 0.5 * (U * U + V * V);
+}
+
+thread_local std::string g_cnn_error = "no error";
+
+}  // namespace
+
+struct lbm_cnn {
+  int H = 0, W = 0, npix = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  float* w = nullptr;        // FP32 master parameters (packed)
+  float* m = nullptr;
+  float* v = nullptr;
+  float* grad = nullptr;
+  __nv_bfloat16* wt[NL] = {};
+  __nv_bfloat16* wb[NL] = {};
+  __nv_bfloat16* act[NL] = {};  // act[0] = input features, act[l] = relu output of layer l-1
+  __nv_bfloat16* dz[2] = {};    // ping-pong output gradients
+  float* xf = nullptr;          // input features FP32 [p][4]
+  float* tf = nullptr;          // target features FP32 [p][4]
+  float* z = nullptr;           // last layer output FP32 [p][4]
+  float* wpartial = nullptr;    // weight-gradient partials
+  double* dpart = nullptr;      // loss / mass partials
+  double* dloss = nullptr;
+  int wchunk = 0, wblocks = 0;
+  long long step = 0;
+  float lr = 1e-3f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  std::string err = "no error";
+};
+
+namespace {
+
+int cfail(lbm_cnn* n, int code, const std::string& msg) {
+  if (n) n->err = msg; else g_cnn_error = msg;
+  return code;
+}
+#define CCK(n, call)                                                              \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess)                                                        \
+      return cfail(n, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));          \
+  } while (0)
+
+int kp_of(int l) { return ru(9 * cin_of(l), 16); }
+int kb_of(int l) { return ru(9 * cout_of(l), 16); }
+
+int pack_all(lbm_cnn* n) {
+  for (int l = 0; l < NL; ++l) {
+    const int cin = cin_of(l), cout = cout_of(l);
+    const int kp = kp_of(l), coutp = ru(cout, 8), kb = kb_of(l), cinp = ru(cin, 8);
+    const int total = std::max(coutp * kp, cinp * kb);
+    k_pack<<<(total + 255) / 256, 256, 0, n->stream>>>(n->w + param_offset(l), cin, cout, kp,
+                                                        coutp, kb, cinp, n->wt[l], n->wb[l]);
+    CCK(n, cudaGetLastError());
+  }
+  return LBM_OK;
+}
+
+template <int CIN, int COUT, int EPI>
+void conv(lbm_cnn* n, const __nv_bfloat16* in, const __nv_bfloat16* wt, const float* bias,
+          const __nv_bfloat16* mask, __nv_bfloat16* ob, float* of) {
+  k_conv<CIN, COUT, EPI><<<(n->npix + 63) / 64, 128, 0, n->stream>>>(in, n->H, n->W, wt, bias,
+                                                                      mask, ob, of);
+}
+
+int forward(lbm_cnn* n, const double* coarse) {
+  k_features<<<(n->npix + 255) / 256, 256, 0, n->stream>>>(coarse, n->npix, n->xf, n->act[0]);
+  const float* w = n->w;
+  conv<4, 32, EPI_RELU_BF16>(n, n->act[0], n->wt[0], w + param_offset(0) + wsize(0), nullptr, n->act[1], nullptr);
+  conv<32, 32, EPI_RELU_BF16>(n, n->act[1], n->wt[1], w + param_offset(1) + wsize(1), nullptr, n->act[2], nullptr);
+  conv<32, 32, EPI_RELU_BF16>(n, n->act[2], n->wt[2], w + param_offset(2) + wsize(2), nullptr, n->act[3], nullptr);
+  conv<32, 32, EPI_RELU_BF16>(n, n->act[3], n->wt[3], w + param_offset(3) + wsize(3), nullptr, n->act[4], nullptr);
+  conv<32, 4, EPI_LINEAR_F32>(n, n->act[4], n->wt[4], w + param_offset(4) + wsize(4), nullptr, nullptr, n->z);
+  CCK(n, cudaGetLastError());
+  return LBM_OK;
+}
+
+template <int CIN, int COUT>
+void wgrad(lbm_cnn* n, const __nv_bfloat16* act, const __nv_bfloat16* dzl, float* grad) {
+  constexpr int NOUT = 9 * CIN * COUT + COUT;
+  const int threads = ru(9 * CIN + COUT, 32);
+  k_wgrad<CIN, COUT><<<n->wblocks, threads, 0, n->stream>>>(act, dzl, n->H, n->W, n->wchunk,
+                                                             n->wpartial);
+  k_sum_partials<<<(NOUT + 255) / 256, 256, 0, n->stream>>>(n->wpartial, n->wblocks, NOUT, grad);
+}
+
+// Loss against the target features and all gradients into n->grad.
+int loss_backward(lbm_cnn* n, const double* target) {
+  k_features<<<(n->npix + 255) / 256, 256, 0, n->stream>>>(target, n->npix, n->tf, nullptr);
+  const int nel = 4 * n->npix, nb = (nel + 255) / 256;
+  k_loss<<<nb, 256, 0, n->stream>>>(n->xf, n->z, n->tf, nel, n->dz[0], n->dpart);
+  k_sum_d<<<1, 32, 0, n->stream>>>(n->dpart, nb, 1.0 / nel, n->dloss);
+  float* g = n->grad;
+  // layer 5 (32 -> 4): dz[0] holds d loss / d z5
+  wgrad<32, 4>(n, n->act[4], n->dz[0], g + param_offset(4));
+  conv<4, 32, EPI_MASK_BF16>(n, n->dz[0], n->wb[4], nullptr, n->act[4], n->dz[1], nullptr);
+  wgrad<32, 32>(n, n->act[3], n->dz[1], g + param_offset(3));
+  conv<32, 32, EPI_MASK_BF16>(n, n->dz[1], n->wb[3], nullptr, n->act[3], n->dz[0], nullptr);
+  wgrad<32, 32>(n, n->act[2], n->dz[0], g + param_offset(2));
+  conv<32, 32, EPI_MASK_BF16>(n, n->dz[0], n->wb[2], nullptr, n->act[2], n->dz[1], nullptr);
+  wgrad<32, 32>(n, n->act[1], n->dz[1], g + param_offset(1));
+  conv<32, 32, EPI_MASK_BF16>(n, n->dz[1], n->wb[1], nullptr, n->act[1], n->dz[0], nullptr);
+  wgrad<4, 32>(n, n->act[0], n->dz[0], g + param_offset(0));
+  CCK(n, cudaGetLastError());
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_cnn_create(int H, int W, void* cuda_stream, lbm_cnn** out) {
+  if (!out) return cfail(nullptr, LBM_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (H < 1 || W < 1 || (long long)H * W > (1ll << 26))
+    return cfail(nullptr, LBM_ERR_INVALID, "bad image size");
+  lbm_cnn* n = new lbm_cnn();
+  n->H = H;
+  n->W = W;
+  n->npix = H * W;
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) n->stream = (cudaStream_t)cuda_stream;
+  else { e = cudaStreamCreate(&n->stream); n->own_stream = true; }
+  const size_t P = n->npix;
+  n->wchunk = 1024;
+  n->wblocks = (int)((P + n->wchunk - 1) / n->wchunk);
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, bytes, n->stream);
+  };
+  A((void**)&n->w, sizeof(float) * LBM_CNN_NPARAMS);
+  A((void**)&n->m, sizeof(float) * LBM_CNN_NPARAMS);
+  A((void**)&n->v, sizeof(float) * LBM_CNN_NPARAMS);
+  A((void**)&n->grad, sizeof(float) * LBM_CNN_NPARAMS);
+  for (int l = 0; l < NL; ++l) {
+    A((void**)&n->wt[l], 2 * (size_t)ru(cout_of(l), 8) * kp_of(l));
+    A((void**)&n->wb[l], 2 * (size_t)ru(cin_of(l), 8) * kb_of(l));
+    A((void**)&n->act[l], 2 * P * CH[l]);
+  }
+  A((void**)&n->dz[0], 2 * P * 32);
+  A((void**)&n->dz[1], 2 * P * 32);
+  A((void**)&n->xf, 4 * P * 4);
+  A((void**)&n->tf, 4 * P * 4);
+  A((void**)&n->z, 4 * P * 4);
+  A((void**)&n->wpartial, sizeof(float) * (size_t)n->wblocks * (9 * 32 * 32 + 32));
+  A((void**)&n->dpart, sizeof(double) * 2 * ((4 * P + 255) / 256 + 1));
+  A((void**)&n->dloss, sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+  if (e != cudaSuccess) {
+    g_cnn_error = std::string("lbm_cnn_create: ") + cudaGetErrorString(e);
+    lbm_cnn_destroy(n);
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+  }
+  if (pack_all(n) != LBM_OK) {
+    g_cnn_error = n->err;
+    lbm_cnn_destroy(n);
+    return LBM_ERR_CUDA;
+  }
+  *out = n;
+  return LBM_OK;
+}
+
+int lbm_cnn_destroy(lbm_cnn* n) {
+  if (!n) return LBM_OK;
+  if (n->stream) cudaStreamSynchronize(n->stream);
+  void* ps[] = {n->w, n->m, n->v, n->grad, n->dz[0], n->dz[1], n->xf, n->tf, n->z,
+                n->wpartial, n->dpart, n->dloss};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  for (int l = 0; l < NL; ++l) {
+    if (n->wt[l]) cudaFree(n->wt[l]);
+    if (n->wb[l]) cudaFree(n->wb[l]);
+    if (n->act[l]) cudaFree(n->act[l]);
+  }
+  if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
+  delete n;
+  return LBM_OK;
+}
+
+int lbm_cnn_set_params(lbm_cnn* n, const float* params, int on_device) {
+  if (!n || !params) return cfail(n, LBM_ERR_INVALID, "NULL argument");
+  CCK(n, cudaMemcpyAsync(n->w, params, sizeof(float) * LBM_CNN_NPARAMS,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, n->stream));
+  CCK(n, cudaMemsetAsync(n->m, 0, sizeof(float) * LBM_CNN_NPARAMS, n->stream));
+  CCK(n, cudaMemsetAsync(n->v, 0, sizeof(float) * LBM_CNN_NPARAMS, n->stream));
+  n->step = 0;
+  const int rc = pack_all(n);
+  if (rc != LBM_OK) return rc;
+  if (!on_device) CCK(n, cudaStreamSynchronize(n->stream));
+  return LBM_OK;
+}
+
+int lbm_cnn_get_params(lbm_cnn* n, float* params, int on_device) {
+  if (!n || !params) return cfail(n, LBM_ERR_INVALID, "NULL argument");
+  CCK(n, cudaMemcpyAsync(params, n->w, sizeof(float) * LBM_CNN_NPARAMS,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, n->stream));
+  if (!on_device) CCK(n, cudaStreamSynchronize(n->stream));
+  return LBM_OK;
+}
+
+int lbm_cnn_set_adam(lbm_cnn* n, double lr, double beta1, double beta2, double eps) {
+  if (!n || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return cfail(n, LBM_ERR_INVALID, "bad Adam hyper-parameters");
+  n->lr = (float)lr; n->b1 = (float)beta1; n->b2 = (float)beta2; n->eps = (float)eps;
+  return LBM_OK;
+}
+
+int lbm_cnn_loss_grad(lbm_cnn* n, const double* coarse, const double* target, double* loss,
+                      float* grads) {
+  if (!n || !coarse || !target) return cfail(n, LBM_ERR_INVALID, "NULL argument");
+  int rc = forward(n, coarse);
+  if (rc == LBM_OK) rc = loss_backward(n, target);
+  if (rc != LBM_OK) return rc;
+  if (loss) CCK(n, cudaMemcpyAsync(loss, n->dloss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+  if (grads)
+    CCK(n, cudaMemcpyAsync(grads, n->grad, sizeof(float) * LBM_CNN_NPARAMS, cudaMemcpyDeviceToHost,
+                           n->stream));
+  CCK(n, cudaStreamSynchronize(n->stream));
+  return LBM_OK;
+}
+
+int lbm_cnn_train_step(lbm_cnn* n, const double* coarse, const double* target, double* loss) {
+  if (!n || !coarse || !target) return cfail(n, LBM_ERR_INVALID, "NULL argument");
+  int rc = forward(n, coarse);
+  if (rc == LBM_OK) rc = loss_backward(n, target);
+  if (rc != LBM_OK) return rc;
+  n->step += 1;
+  const float c1 = 1.f - powf(n->b1, (float)n->step), c2 = 1.f - powf(n->b2, (float)n->step);
+  k_adam<<<(LBM_CNN_NPARAMS + 255) / 256, 256, 0, n->stream>>>(n->w, n->m, n->v, n->grad,
+                                                               LBM_CNN_NPARAMS, n->lr, n->b1,
+                                                               n->b2, n->eps, c1, c2);
+  CCK(n, cudaGetLastError());
+  rc = pack_all(n);
+  if (rc != LBM_OK) return rc;
+  if (loss) {
+    CCK(n, cudaMemcpyAsync(loss, n->dloss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+    CCK(n, cudaStreamSynchronize(n->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_cnn_correct(lbm_cnn* n, const double* coarse, double* corrected, double mass_tol,
+                    int* used_fallback) {
+  if (!n || !coarse || !corrected) return cfail(n, LBM_ERR_INVALID, "NULL argument");
+  int rc = forward(n, coarse);
+  if (rc != LBM_OK) return rc;
+  const int nb = (n->npix + 255) / 256;
+  k_apply<<<nb, 256, 0, n->stream>>>(n->xf, n->z, n->npix, corrected, coarse, n->dpart);
+  CCK(n, cudaGetLastError());
+  std::vector<double> part(2 * (size_t)nb);
+  CCK(n, cudaMemcpyAsync(part.data(), n->dpart, sizeof(double) * part.size(),
+                         cudaMemcpyDeviceToHost, n->stream));
+  CCK(n, cudaStreamSynchronize(n->stream));
+  double m1 = 0, m0 = 0;
+  for (int b = 0; b < nb; ++b) { m1 += part[2 * b]; m0 += part[2 * b + 1]; }
+  const bool fallback = !std::isfinite(m1) || std::fabs(m1 - m0) > mass_tol * std::fabs(m0);
+  if (fallback) {
+    CCK(n, cudaMemcpyAsync(corrected, coarse, sizeof(double) * 4 * n->npix,
+                           cudaMemcpyDeviceToDevice, n->stream));
+    CCK(n, cudaStreamSynchronize(n->stream));
+  }
+  if (used_fallback) *used_fallback = fallback ? 1 : 0;
+  return LBM_OK;
+}
+
+int lbm_restrict(const double* fine, int Hf, int Wf, int r, double* coarse, void* cuda_stream) {
+  if (!fine || !coarse || r < 1 || Hf < r || Wf < r || Hf % r || Wf % r)
+    return cfail(nullptr, LBM_ERR_INVALID, "lbm_restrict: bad sizes");
+  const int nc = (Hf / r) * (Wf / r);
+  k_restrict<<<(nc + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(fine, Hf, Wf, r, coarse);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cfail(nullptr, LBM_ERR_CUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+const char* lbm_cnn_last_error(lbm_cnn* n) { return n ? n->err.c_str() : g_cnn_error.c_str(); }
+
+}  // extern "C"

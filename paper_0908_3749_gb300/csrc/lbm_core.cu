@@ -17,6 +17,7 @@
 //   -> store; epilogue: watchdog flags and, every audit_every steps, block
 //   partial sums of (rho, j, e) in FP64 with a fixed-order final pass done by
 //   the last block to finish (no floating-point atomics).
+#include <cuda.h>  // CUtensorMap (the encoder is fetched at run time; libcuda is not linked)
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -52,6 +53,8 @@ struct DevStatus {
   unsigned long long first_bad;   // first level with non-finite / rho <= 0
   unsigned long long first_negT;  // first level with T <= 0
   unsigned long long audit_count; // fused audits written so far
+  int tma_timeout;                // a tile load did not complete in time
+  int pad2;
   double audit_now[4];            // result of the standalone audit
   double audit_totals[LBM_AUDIT_RING][4];
   long long audit_steps[LBM_AUDIT_RING];
@@ -130,13 +133,14 @@ __device__ __forceinline__ double final_sum4(const double* partial, int nblocks,
 // Boundary ghosts
 // ---------------------------------------------------------------------------
 template <typename R, typename Off>
-__device__ __forceinline__ Cons<R> load_cons(const R* __restrict__ fin, Off plane, Off idx) {
+__device__ __forceinline__ Cons<R> load_cons(const Coeffs<R>& K, const R* __restrict__ fin,
+                                             Off plane, Off idx) {
   R f[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) f[i] = fin[i * plane + idx];
   Groups<R> d;
   transform(f, d);
-  return conserved(d);
+  return conserved(K, d);
 }
 
 // Ghost populations outside `side` of the node with conserved moments `own`.
@@ -161,7 +165,7 @@ __device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict_
     s.jy = own.rho * v;
     s.e = own.rho * T + R(0.5) * own.rho * (u * u + v * v);
   } else {  // LBM_BC_EXTRAP
-    const Cons<R> in = has_inward ? load_cons(fin, plane, inward) : own;
+    const Cons<R> in = has_inward ? load_cons(A.K, fin, plane, inward) : own;
     const R r1 = recip(own.rho), r2 = recip(in.rho);
     const R u1 = own.jx * r1, v1 = own.jy * r1, u2 = in.jx * r2, v2 = in.jy * r2;
     const R T1 = own.e * r1 - R(0.5) * (u1 * u1 + v1 * v1);
@@ -180,41 +184,125 @@ __device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict_
 }
 
 // ---------------------------------------------------------------------------
+// Tile loads: TMA (cp.async.bulk.tensor) into shared memory, mbarrier-tracked
+// ---------------------------------------------------------------------------
+// The populations are a 3D tensor (x: pitch, y: ny, i: 16). A block's tile is
+// its BX x BY nodes plus a halo: rows y0-1 .. y0+BY, columns x0-4 .. x0+BX+3
+// (4 columns instead of 1 so that the box starts on a 16-byte boundary), all
+// 16 populations, landing in shared memory as [16][BY+2][BX+8]. Boxes that
+// reach outside the tensor are filled with zeros; those values are never
+// used (boundary nodes take ghosts, periodic wraps read global memory).
+constexpr int HALO_X = 4;
+template <typename R>
+struct Tile {
+  static constexpr int BXP = Shape<R>::X + 2 * HALO_X;
+  static constexpr int ROWS = Shape<R>::Y + 2;
+  static constexpr int ELEMS = 16 * ROWS * BXP;
+  static constexpr unsigned BYTES = ELEMS * sizeof(R);
+};
+constexpr long long TMA_WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the barrier for at most `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  long long limit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > limit) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map, int x, int y,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(0), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // The fused step
 // ---------------------------------------------------------------------------
 // Off: unsigned (32-bit element offsets, grids with 16 * plane < 2^32) or
-// long long. One thread per node.
+// long long. One thread per node; the block's tile and halo come in by one
+// TMA copy, the stencil reads shared memory.
 template <typename R, typename Off>
 __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
-    k_step(const R* __restrict__ fin, R* __restrict__ fout, const StepArgs<R> A) {
+    k_step(const __grid_constant__ CUtensorMap tmap, const R* __restrict__ fin,
+           R* __restrict__ fout, const StepArgs<R> A) {
   constexpr int BXD = Shape<R>::X, BYD = Shape<R>::Y, N = BXD * BYD;
+  constexpr int BXP = Tile<R>::BXP, ROWS = Tile<R>::ROWS;
+  __shared__ __align__(128) R tile[Tile<R>::ELEMS];
   __shared__ double sm[N / 4][4];
+  __shared__ unsigned long long bar;
   __shared__ unsigned long long s_step;
-  __shared__ int s_last;
+  __shared__ int s_audit, s_last;
   const int t = threadIdx.y * BXD + threadIdx.x;
+  const int x0 = blockIdx.x * BXD, y0 = blockIdx.y * BYD;
   if (t == 0) {
+    // Start the tile copy first so that its latency overlaps the read of
+    // the step counter.
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, Tile<R>::BYTES);
+    tma_load_tile(tile, &tmap, x0 - HALO_X, y0 - 1, &bar);
     const unsigned long long done = *(volatile unsigned long long*)&A.st->blocks_done;
-    s_step = done / (unsigned long long)A.nblocks;
+    const unsigned long long step = done / (unsigned long long)A.nblocks;
+    s_step = step;
+    s_audit = A.audit_every > 0 && (step % (unsigned long long)A.audit_every) == 0;
   }
   __syncthreads();
   const unsigned long long step = s_step;
-  const bool audit = A.audit_every > 0 && (step % (unsigned long long)A.audit_every) == 0;
+  const bool audit = s_audit != 0;
+  // Every thread waits for the tile (bounded); the block decides together.
+  if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, TMA_WAIT_CYCLES))) {
+    // The copy did not land: record it, give it a second bounded wait so that
+    // no copy is left writing into shared memory, and leave without output.
+    if (t == 0) atomicExch(&A.st->tma_timeout, 1);
+    mbar_wait_bounded(&bar, 0, TMA_WAIT_CYCLES);
+    return;
+  }
 
-  const int x = blockIdx.x * BXD + threadIdx.x;
-  const int y = blockIdx.y * BYD + threadIdx.y;
+  const int x = x0 + threadIdx.x;
+  const int y = y0 + threadIdx.y;
   const bool active = x < A.nx && y < A.ny;
-  double tot[4] = {0.0, 0.0, 0.0, 0.0};
+  R cons[4] = {R(0), R(0), R(0), R(0)};  // widened to FP64 on audit steps only
   bool bad = false, negT = false;
 
   if (active) {
     const Off P = (Off)A.plane, pitch = (Off)A.pitch;
     const Off c = (Off)y * pitch + (Off)x;
+    const R* ctr = tile + (threadIdx.y + 1) * BXP + threadIdx.x + HALO_X;  // + i * ROWS * BXP
+    constexpr int PS = ROWS * BXP;
     R f[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) f[i] = fin[i * P + c];
+    for (int i = 0; i < 16; ++i) f[i] = ctr[i * PS];
     Groups<R> d;
     transform(f, d);
-    const Cons<R> m = conserved(d);
+    const Cons<R> m = conserved(A.K, d);
     R acc[16];
     const R press = collide(A.K, d, m, acc);
 #pragma unroll
@@ -222,14 +310,31 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
 
     bad = !(m.rho > R(0)) || !isfinite(m.rho + m.jx + m.jy + m.e);
     negT = !bad && !(press > R(0));
-    if (audit) {
-      tot[0] = (double)m.rho; tot[1] = (double)m.jx;
-      tot[2] = (double)m.jy;  tot[3] = (double)m.e;
-    }
+    cons[0] = m.rho; cons[1] = m.jx; cons[2] = m.jy; cons[3] = m.e;
 
+    if (x > 0 && x < A.nx - 1 && y > 0 && y < A.ny - 1) {
+      // interior node: all four neighbours are in the tile
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        R a = acc[i];
+        if (has_x(i)) {
+          a += A.K.aW[i] * ctr[i * PS - 1];
+          a += A.K.aE[i] * ctr[i * PS + 1];
+        }
+        if (has_y(i)) {
+          a += A.K.aS[i] * ctr[i * PS - BXP];
+          a += A.K.aN[i] * ctr[i * PS + BXP];
+        }
+        acc[i] = a;
+      }
+    } else {
     // x- neighbour (west)
-    if (x > 0 || A.bc[0] == LBM_BC_PERIODIC) {
-      const Off n = (x > 0) ? c - 1 : c + (Off)(A.nx - 1);
+    if (x > 0) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_x(i)) acc[i] += A.K.aW[i] * ctr[i * PS - 1];
+    } else if (A.bc[0] == LBM_BC_PERIODIC) {
+      const Off n = c + (Off)(A.nx - 1);
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         if (has_x(i)) acc[i] += A.K.aW[i] * fin[i * P + n];
@@ -241,8 +346,12 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
         if (has_x(i)) acc[i] += A.K.aW[i] * g[i];
     }
     // x+ neighbour (east)
-    if (x < A.nx - 1 || A.bc[1] == LBM_BC_PERIODIC) {
-      const Off n = (x < A.nx - 1) ? c + 1 : c - (Off)(A.nx - 1);
+    if (x < A.nx - 1) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_x(i)) acc[i] += A.K.aE[i] * ctr[i * PS + 1];
+    } else if (A.bc[1] == LBM_BC_PERIODIC) {
+      const Off n = c - (Off)(A.nx - 1);
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         if (has_x(i)) acc[i] += A.K.aE[i] * fin[i * P + n];
@@ -254,8 +363,12 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
         if (has_x(i)) acc[i] += A.K.aE[i] * g[i];
     }
     // y- neighbour (south)
-    if (y > 0 || A.bc[2] == LBM_BC_PERIODIC) {
-      const Off n = (y > 0) ? c - pitch : c + (Off)(A.ny - 1) * pitch;
+    if (y > 0) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_y(i)) acc[i] += A.K.aS[i] * ctr[i * PS - BXP];
+    } else if (A.bc[2] == LBM_BC_PERIODIC) {
+      const Off n = c + (Off)(A.ny - 1) * pitch;
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         if (has_y(i)) acc[i] += A.K.aS[i] * fin[i * P + n];
@@ -267,8 +380,12 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
         if (has_y(i)) acc[i] += A.K.aS[i] * g[i];
     }
     // y+ neighbour (north)
-    if (y < A.ny - 1 || A.bc[3] == LBM_BC_PERIODIC) {
-      const Off n = (y < A.ny - 1) ? c + pitch : c - (Off)(A.ny - 1) * pitch;
+    if (y < A.ny - 1) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (has_y(i)) acc[i] += A.K.aN[i] * ctr[i * PS + BXP];
+    } else if (A.bc[3] == LBM_BC_PERIODIC) {
+      const Off n = c - (Off)(A.ny - 1) * pitch;
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         if (has_y(i)) acc[i] += A.K.aN[i] * fin[i * P + n];
@@ -279,6 +396,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
       for (int i = 0; i < 16; ++i)
         if (has_y(i)) acc[i] += A.K.aN[i] * g[i];
     }
+    }  // boundary node
 #pragma unroll
     for (int i = 0; i < 16; ++i) fout[i * P + c] = acc[i];
   }
@@ -296,6 +414,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
     if (t == 0) atomicAdd(&A.st->blocks_done, 1ull);
     return;
   }
+  const double tot[4] = {(double)cons[0], (double)cons[1], (double)cons[2], (double)cons[3]};
   const double bs = block_sum4<N>(tot, sm);
   if (t < 4) A.partial[4 * bid + t] = bs;
   __syncthreads();
@@ -344,7 +463,7 @@ __global__ void k_init(R* __restrict__ f, const double* __restrict__ rho,
 template <typename R>
 __global__ void k_moments(const R* __restrict__ f, double* rho, double* u,
                           double* v, double* T, int nx, int ny, long long pitch,
-                          long long plane) {
+                          long long plane, const Coeffs<double> K) {
   const int x = blockIdx.x * AUX_X + threadIdx.x;
   const int y = blockIdx.y * AUX_Y + threadIdx.y;
   if (x >= nx || y >= ny) return;
@@ -354,7 +473,7 @@ __global__ void k_moments(const R* __restrict__ f, double* rho, double* u,
   for (int i = 0; i < 16; ++i) g[i] = (double)f[i * plane + c];
   Groups<double> d;
   transform(g, d);
-  const Cons<double> m = conserved(d);
+  const Cons<double> m = conserved(K, d);
   const double r = 1.0 / m.rho;
   const double uu = m.jx * r, vv = m.jy * r;
   const long long k = (long long)y * nx + x;
@@ -368,7 +487,8 @@ template <typename R>
 __global__ void __launch_bounds__(AUX_N) k_audit(const R* __restrict__ f, int nx,
                                                  int ny, long long pitch,
                                                  long long plane, double area,
-                                                 DevStatus* st, double* partial) {
+                                                 DevStatus* st, double* partial,
+                                                 const Coeffs<double> K) {
   __shared__ double sm[AUX_N / 4][4];
   __shared__ int s_last;
   const int x = blockIdx.x * AUX_X + threadIdx.x;
@@ -382,7 +502,7 @@ __global__ void __launch_bounds__(AUX_N) k_audit(const R* __restrict__ f, int nx
     for (int i = 0; i < 16; ++i) g[i] = (double)f[i * plane + c];
     Groups<double> d;
     transform(g, d);
-    const Cons<double> m = conserved(d);
+    const Cons<double> m = conserved(K, d);
     tot[0] = m.rho; tot[1] = m.jx; tot[2] = m.jy; tot[3] = m.e;
   }
   const int nblocks = gridDim.x * gridDim.y;
@@ -445,6 +565,7 @@ bool invert(int n, const double* a, double* out) {
 }
 
 bool build_coeffs(const lbm_config& cfg, Coeffs<double>& K) {
+  fill_forward(K);
   double m0[16], mx[16], my[16], mc[4], ms[4];
   for (int r = 0; r < 4; ++r)
     for (int g = 0; g < 4; ++g) {
@@ -533,6 +654,7 @@ struct lbm_ctx {
   dim3 grid, aux_grid;  // step grid; init / moments / audit grid
   bool wide = false;    // 64-bit element offsets needed
   Coeffs<double> Kd;
+  CUtensorMap tmap[2];        // TMA descriptors of the two population buffers
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   std::string err = "no error";
 };
@@ -580,18 +702,19 @@ StepArgs<R> make_args(lbm_ctx* c) {
 
 int launch_step(lbm_ctx* c, cudaStream_t s, int from) {
   const int to = 1 - from;
+  const CUtensorMap& tm = c->tmap[from];
   if (c->esize == 8) {
     const dim3 blk(Shape<double>::X, Shape<double>::Y);
     const double* fi = (const double*)c->f[from];
     double* fo = (double*)c->f[to];
-    if (c->wide) k_step<double, long long><<<c->grid, blk, 0, s>>>(fi, fo, make_args<double>(c));
-    else k_step<double, unsigned><<<c->grid, blk, 0, s>>>(fi, fo, make_args<double>(c));
+    if (c->wide) k_step<double, long long><<<c->grid, blk, 0, s>>>(tm, fi, fo, make_args<double>(c));
+    else k_step<double, unsigned><<<c->grid, blk, 0, s>>>(tm, fi, fo, make_args<double>(c));
   } else {
     const dim3 blk(Shape<float>::X, Shape<float>::Y);
     const float* fi = (const float*)c->f[from];
     float* fo = (float*)c->f[to];
-    if (c->wide) k_step<float, long long><<<c->grid, blk, 0, s>>>(fi, fo, make_args<float>(c));
-    else k_step<float, unsigned><<<c->grid, blk, 0, s>>>(fi, fo, make_args<float>(c));
+    if (c->wide) k_step<float, long long><<<c->grid, blk, 0, s>>>(tm, fi, fo, make_args<float>(c));
+    else k_step<float, unsigned><<<c->grid, blk, 0, s>>>(tm, fi, fo, make_args<float>(c));
   }
   CK(c, cudaGetLastError());
   return LBM_OK;
@@ -612,6 +735,43 @@ int ensure_graph(lbm_ctx* c, int from) {
   e = cudaGraphInstantiate(&c->graph[from], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  return LBM_OK;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// Tensor map of one population buffer: dims (pitch, ny, 16), box = one tile
+// with its halo.
+int encode_tile_map(lbm_ctx* c, int b) {
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) return fail(c, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const bool dbl = c->esize == 8;
+  const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->cfg.ny, 16};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->esize, (cuuint64_t)c->plane * c->esize};
+  const cuuint32_t box[3] = {(cuuint32_t)(dbl ? Tile<double>::BXP : Tile<float>::BXP),
+                             (cuuint32_t)(dbl ? Tile<double>::ROWS : Tile<float>::ROWS), 16};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(&c->tmap[b], dbl ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                         3, c->f[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return LBM_OK;
 }
 
@@ -728,7 +888,8 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
     lbm_destroy(c);
     return rc;
   }
-  if (reset_status(c, 0) != LBM_OK) {
+  if (encode_tile_map(c, 0) != LBM_OK || encode_tile_map(c, 1) != LBM_OK ||
+      reset_status(c, 0) != LBM_OK) {
     g_create_error = c->err;
     lbm_destroy(c);
     return LBM_ERR_CUDA;
@@ -790,11 +951,11 @@ int lbm_moments(lbm_ctx* c, double* rho, double* u, double* v, double* T, int on
   if (c->esize == 8)
     k_moments<double><<<c->aux_grid, blk, 0, c->stream>>>((const double*)c->f[c->cur], d[0], d[1],
                                                        d[2], d[3], c->cfg.nx, c->cfg.ny,
-                                                       c->pitch, c->plane);
+                                                       c->pitch, c->plane, c->Kd);
   else
     k_moments<float><<<c->aux_grid, blk, 0, c->stream>>>((const float*)c->f[c->cur], d[0], d[1],
                                                       d[2], d[3], c->cfg.nx, c->cfg.ny,
-                                                      c->pitch, c->plane);
+                                                      c->pitch, c->plane, c->Kd);
   CK(c, cudaGetLastError());
   if (!on_device) {
     for (int k = 0; k < 4; ++k)
@@ -828,11 +989,11 @@ int lbm_audit(lbm_ctx* c, double totals[4]) {
   if (c->esize == 8)
     k_audit<double><<<c->aux_grid, blk, 0, c->stream>>>((const double*)c->f[c->cur], c->cfg.nx,
                                                      c->cfg.ny, c->pitch, c->plane, area,
-                                                     c->st, c->partial);
+                                                     c->st, c->partial, c->Kd);
   else
     k_audit<float><<<c->aux_grid, blk, 0, c->stream>>>((const float*)c->f[c->cur], c->cfg.nx,
                                                     c->cfg.ny, c->pitch, c->plane, area,
-                                                    c->st, c->partial);
+                                                    c->st, c->partial, c->Kd);
   CK(c, cudaGetLastError());
   CK(c, cudaMemcpyAsync(totals, c->st->audit_now, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                         c->stream));
@@ -865,6 +1026,10 @@ int lbm_status(lbm_ctx* c, long long* first_bad_step, long long* first_negT_step
   CK(c, cudaMemcpyAsync(&h, c->st, offsetof(DevStatus, audit_totals), cudaMemcpyDeviceToHost,
                         c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  if (h.tma_timeout) {
+    c->err = "a tile load (TMA) did not complete within its time limit";
+    return LBM_ERR_TIMEOUT;
+  }
   const long long bad = h.first_bad == NONE ? -1 : (long long)h.first_bad;
   const long long neg = h.first_negT == NONE ? -1 : (long long)h.first_negT;
   if (first_bad_step) *first_bad_step = bad;

@@ -147,21 +147,22 @@ __device__ __forceinline__ void tube_tile(const BatchArgs& A, const float* __res
       for (int i = 0; i < 16; ++i) f[i] = fin[i * P + c];
       Groups<float> d;
       transform(f, d);
-      const Cons<float> m = conserved(d);
+      const Cons<float> m = conserved(A.E, d);
       const Eq<float> q = equilibria(m.rho, m.jx, m.jy, m.e);
       // deviations from equilibrium of the non-conserved moments, relaxed
-      const float r11 = w[6] * (dot4<TabS>(2, d.S) - q.m11);
-      const float r12 = w[7] * dot4<TabS>(3, d.S);
-      const float r7 = w[2] * (dot4<TabX>(1, d.X) - q.m7);
-      const float r9 = w[4] * (dot4<TabX>(2, d.X) - q.m9);
-      const float r15 = w[10] * dot4<TabX>(3, d.X);
-      const float r8 = w[3] * (dot4<TabY>(1, d.Y) - q.m8);
-      const float r10 = w[5] * (dot4<TabY>(2, d.Y) - q.m10);
-      const float r16 = w[11] * dot4<TabY>(3, d.Y);
-      const float r5 = w[0] * (float(bc2(0, 0)) * d.C[0] + float(bc2(0, 1)) * d.C[1] - q.m5);
-      const float r13 = w[8] * (float(bc2(1, 0)) * d.C[0] + float(bc2(1, 1)) * d.C[1] - q.m13);
-      const float r6 = w[1] * (float(bs2(0, 0)) * d.C[2] + float(bs2(0, 1)) * d.C[3] - q.m6);
-      const float r14 = w[9] * (float(bs2(1, 0)) * d.C[2] + float(bs2(1, 1)) * d.C[3] - q.m14);
+      const Coeffs<float>& E = A.E;
+      const float r11 = w[6] * (row4(E.F0, 2, d.S) - q.m11);
+      const float r12 = w[7] * row4(E.F0, 3, d.S);
+      const float r7 = w[2] * (row4(E.FX, 1, d.X) - q.m7);
+      const float r9 = w[4] * (row4(E.FX, 2, d.X) - q.m9);
+      const float r15 = w[10] * row4(E.FX, 3, d.X);
+      const float r8 = w[3] * (row4(E.FY, 1, d.Y) - q.m8);
+      const float r10 = w[5] * (row4(E.FY, 2, d.Y) - q.m10);
+      const float r16 = w[11] * row4(E.FY, 3, d.Y);
+      const float r5 = w[0] * (E.FC[0][0] * d.C[0] + E.FC[0][1] * d.C[1] - q.m5);
+      const float r13 = w[8] * (E.FC[1][0] * d.C[0] + E.FC[1][1] * d.C[1] - q.m13);
+      const float r6 = w[1] * (E.FS[0][0] * d.C[2] + E.FS[0][1] * d.C[3] - q.m6);
+      const float r14 = w[9] * (E.FS[1][0] * d.C[2] + E.FS[1][1] * d.C[3] - q.m14);
       float S[4], C[4], X[4], Y[4], df[16];
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
@@ -257,7 +258,7 @@ __global__ void k_tubes_init(float* f, const TubeDesc* tubes, const int2* items,
 
 __global__ void k_tubes_moments(const float* f, const TubeDesc* tubes, const int2* items,
                                 long long P, int tile, double* rho, double* u, double* v,
-                                double* T) {
+                                double* T, const Coeffs<double> K) {
   const int2 it = items[blockIdx.x];
   const TubeDesc D = tubes[it.x];
   for (int j = threadIdx.x; j < tile; j += blockDim.x) {
@@ -268,7 +269,7 @@ __global__ void k_tubes_moments(const float* f, const TubeDesc* tubes, const int
     for (int i = 0; i < 16; ++i) g[i] = (double)f[i * P + D.off + x];
     Groups<double> d;
     transform(g, d);
-    const Cons<double> m = conserved(d);
+    const Cons<double> m = conserved(K, d);
     const double r = 1.0 / m.rho, uu = m.jx * r, vv = m.jy * r;
     const long long k = D.out + x;
     if (rho) rho[k] = m.rho;
@@ -281,7 +282,7 @@ __global__ void k_tubes_moments(const float* f, const TubeDesc* tubes, const int
 // One block per tube: FP64 totals over the tube's nodes in a fixed order.
 __global__ void __launch_bounds__(AUX_T) k_tubes_audit(const float* f, const TubeDesc* tubes,
                                                        const double* dx, long long P,
-                                                       double* totals) {
+                                                       double* totals, const Coeffs<double> K) {
   __shared__ double sm[AUX_T][4];
   const TubeDesc D = tubes[blockIdx.x];
   double s[4] = {0.0, 0.0, 0.0, 0.0};
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(AUX_T) k_tubes_audit(const float* f, const Tub
     for (int i = 0; i < 16; ++i) g[i] = (double)f[i * P + D.off + x];
     Groups<double> d;
     transform(g, d);
-    const Cons<double> m = conserved(d);
+    const Cons<double> m = conserved(K, d);
     s[0] += m.rho; s[1] += m.jx; s[2] += m.jy; s[3] += m.e;
   }
 #pragma unroll
@@ -386,6 +387,7 @@ bool lattice_constants(Coeffs<double>& K) {
       !invert_small(2, mc, ic) || !invert_small(2, ms, is))
     return false;
   memset(&K, 0, sizeof(K));
+  fill_forward(K);
   const double sx[4] = {0.5, 0.5, 0.25, 0.25};
   for (int g = 0; g < 4; ++g)
     for (int c = 0; c < 4; ++c) {
@@ -688,7 +690,7 @@ int lbm_batch_moments(lbm_batch* b, double* rho, double* u, double* v, double* T
   BCK(b, cudaStreamSynchronize(b->stream));
   const int tile = VARIANTS[b->variant].tile;
   k_tubes_moments<<<b->nitems, AUX_T, 0, b->stream>>>(b->f[hs.cur], b->tubes, b->items,
-                                                       b->plane, tile, d[0], d[1], d[2], d[3]);
+                                                       b->plane, tile, d[0], d[1], d[2], d[3], b->Kd);
   BCK(b, cudaGetLastError());
   if (!on_device) {
     for (int k = 0; k < 4; ++k)
@@ -706,7 +708,7 @@ int lbm_batch_audit(lbm_batch* b, double* totals) {
   BCK(b, cudaMemcpyAsync(&hs, b->st, sizeof(hs), cudaMemcpyDeviceToHost, b->stream));
   BCK(b, cudaStreamSynchronize(b->stream));
   k_tubes_audit<<<b->ntubes, AUX_T, 0, b->stream>>>(b->f[hs.cur], b->tubes, b->d_dx, b->plane,
-                                                     b->d_totals);
+                                                     b->d_totals, b->Kd);
   BCK(b, cudaGetLastError());
   BCK(b, cudaMemcpyAsync(totals, b->d_totals, sizeof(double) * 4 * b->ntubes,
                          cudaMemcpyDeviceToHost, b->stream));

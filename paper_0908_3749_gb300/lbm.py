@@ -355,3 +355,95 @@ def lbm_batch_destroy(b):
 
 def lbm_batch_last_error(b=None):
     return load().lbm_batch_last_error(b).decode()
+
+
+# ----------------------------------------------------------------------------
+# Learned coarse-grid corrector (include/lbm_cnn.h)
+# ----------------------------------------------------------------------------
+CNN_NPARAMS = 30084
+CNN_CHANNELS = (4, 32, 32, 32, 32, 4)
+
+_SIGS.update({
+    "lbm_cnn_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "lbm_cnn_destroy": (ctypes.c_int, [_vp]),
+    "lbm_cnn_set_params": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "lbm_cnn_get_params": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "lbm_cnn_set_adam": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "lbm_cnn_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "lbm_cnn_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "lbm_cnn_correct": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_restrict": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "lbm_cnn_last_error": (ctypes.c_char_p, [_vp]),
+})
+
+
+def _ccheck(rc, n=None):
+    if rc != LBM_OK:
+        raise LBMError(rc, load().lbm_cnn_last_error(n).decode())
+    return rc
+
+
+def _dev(t):
+    p, d = _ptr(t)
+    if not d:
+        raise ValueError("expected a CUDA tensor")
+    return p
+
+
+def lbm_cnn_create(H, W, stream=None):
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = _vp()
+    _ccheck(load().lbm_cnn_create(int(H), int(W), _vp(stream or None), ctypes.byref(out)))
+    return out.value
+
+
+def lbm_cnn_destroy(n):
+    if n:
+        _ccheck(load().lbm_cnn_destroy(n))
+
+
+def lbm_cnn_set_params(n, params):
+    p, d = _ptr(params)
+    _ccheck(load().lbm_cnn_set_params(n, p, d), n)
+
+
+def lbm_cnn_get_params(n, out):
+    p, d = _ptr(out)
+    _ccheck(load().lbm_cnn_get_params(n, p, d), n)
+
+
+def lbm_cnn_set_adam(n, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    _ccheck(load().lbm_cnn_set_adam(n, lr, beta1, beta2, eps), n)
+
+
+def lbm_cnn_loss_grad(n, coarse, target, grads=None):
+    """(loss, grads) for device field tensors [4][H][W]; grads: host float32
+    array of CNN_NPARAMS (allocated when None)."""
+    import numpy as np
+    if grads is None:
+        grads = np.empty(CNN_NPARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _ccheck(load().lbm_cnn_loss_grad(n, _dev(coarse), _dev(target), ctypes.byref(loss),
+                                     grads.ctypes.data), n)
+    return loss.value, grads
+
+
+def lbm_cnn_train_step(n, coarse, target, want_loss=True):
+    loss = ctypes.c_double()
+    _ccheck(load().lbm_cnn_train_step(n, _dev(coarse), _dev(target),
+                                      ctypes.byref(loss) if want_loss else None), n)
+    return loss.value if want_loss else None
+
+
+def lbm_cnn_correct(n, coarse, out, mass_tol=1e-2):
+    fb = ctypes.c_int()
+    _ccheck(load().lbm_cnn_correct(n, _dev(coarse), _dev(out), float(mass_tol), ctypes.byref(fb)), n)
+    return bool(fb.value)
+
+
+def lbm_restrict(fine, r, out, stream=None):
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    Hf, Wf = int(fine.shape[-2]), int(fine.shape[-1])
+    _ccheck(load().lbm_restrict(_dev(fine), Hf, Wf, int(r), _dev(out), _vp(stream or None)))
