@@ -165,6 +165,31 @@ int lbm_element_size(lbm_ctx* ctx);
  * failure on this thread when ctx is NULL). Never NULL. */
 const char* lbm_last_error(lbm_ctx* ctx);
 
+/* Conservation totals without any device allocation. The paper has no
+ * counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory (an allocator-free embedding, a fully reserved
+ * memory pool, a loop that must not allocate): it computes the same totals
+ * as lbm_audit -- (sum rho, sum j_x, sum j_y, sum e) x dx x dy in FP64 -- of a
+ * population array the caller owns, using a fixed scratch array that the
+ * library holds in device global memory (one partial sum per block of 32 x 8
+ * nodes, LBM_NOALLOC_MAX_BLOCKS blocks: 128 KiB per device, kept until the
+ * process exits).
+ *  f         device pointer, populations [16][ny][pitch] (x fastest), FP64
+ *            (precision LBM_FP64) or FP32 (LBM_FP32); only x < nx is read
+ *  totals    device pointer to 4 doubles, written by the kernel
+ *  cuda_stream  the stream to run on (NULL: legacy default stream)
+ * Returns LBM_ERR_INVALID for bad arguments or a grid that needs more than
+ * LBM_NOALLOC_MAX_BLOCKS blocks (more than ~1.05e6 nodes); the reason is in
+ * lbm_audit_noalloc_last_error(). Asynchronous. All calls share the scratch:
+ * calls whose kernels overlap on the GPU (different streams or host threads)
+ * race and give wrong totals, so issue them one after another in one stream.
+ * The first call on a device looks up the scratch's device address; make it
+ * before any stream capture that includes this entry point. */
+#define LBM_NOALLOC_MAX_BLOCKS 4096
+int lbm_audit_noalloc(const void* f, int precision, int nx, int ny, long long pitch,
+                      double dx, double dy, double* totals, void* cuda_stream);
+const char* lbm_audit_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

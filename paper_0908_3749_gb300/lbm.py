@@ -115,6 +115,13 @@ def _ptr(a):
     return a.ctypes.data, 0
 
 
+def _dev(t):
+    p, d = _ptr(t)
+    if not d:
+        raise ValueError("expected a CUDA tensor")
+    return p
+
+
 def make_config(nx, ny, dx, dy, dt, s, bc, precision="fp64", audit_every=0,
                 internal_dof=0):
     """lbm_config from plain values; ``bc`` is four (kind, state) pairs for
@@ -247,6 +254,24 @@ _BATCH_SIGS = {
     "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
 }
 _SIGS.update(_BATCH_SIGS)
+_SIGS.update({
+    "lbm_audit_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ll,
+                                         ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "lbm_audit_noalloc_last_error": (ctypes.c_char_p, []),
+})
+NOALLOC_MAX_BLOCKS = 4096
+
+
+def lbm_audit_noalloc(f, precision, nx, ny, pitch, dx, dy, totals, stream=None):
+    """Allocation-free conservation totals of a caller-owned device
+    population tensor into a caller-owned device tensor of 4 doubles."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rc = load().lbm_audit_noalloc(_dev(f), prec, int(nx), int(ny), int(pitch), float(dx),
+                                  float(dy), _dev(totals), _vp(stream or None))
+    if rc != LBM_OK:
+        raise LBMError(rc, load().lbm_audit_noalloc_last_error().decode())
 _KEEP = {}
 
 
@@ -381,13 +406,6 @@ def _ccheck(rc, n=None):
     if rc != LBM_OK:
         raise LBMError(rc, load().lbm_cnn_last_error(n).decode())
     return rc
-
-
-def _dev(t):
-    p, d = _ptr(t)
-    if not d:
-        raise ValueError("expected a CUDA tensor")
-    return p
 
 
 def lbm_cnn_create(H, W, stream=None):
