@@ -53,9 +53,13 @@ enum lbm_precision {
                         reported moments (conserved sums, temperature) and
                         the conservation audits */
   LBM_TC_BF16X3 = 2, /* FP32 populations, 16x16 transforms as split-BF16
-                        tensor-core products (reserved) */
-  LBM_TC_TF32X3 = 3  /* FP32 populations, transforms as 3xTF32 tensor-core
-                        products (reserved) */
+                        tensor-core products (reserved: LBM_ERR_UNSUPPORTED) */
+  LBM_TC_TF32X3 = 3  /* FP32 populations; m = M f and the back-map M^-1 as
+                        3xTF32 tensor-core products (tcgen05, FP32
+                        accumulation) over 128-node tiles; equilibria,
+                        Lax-Wendroff update, moments and audits as LBM_FP32.
+                        Grids with 16 x pitch x ny >= 2^32 elements are
+                        LBM_ERR_UNSUPPORTED. */
 };
 
 /* Boundary kinds (Sec. V). The ghost node outside a side holds

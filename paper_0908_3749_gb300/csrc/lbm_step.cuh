@@ -1,0 +1,381 @@
+// lbm_step.cuh -- device code shared by the fused step kernels (FP64/FP32 in
+// lbm_core.cu, tensor-core in lbm_tc.cu): status block and kernel arguments,
+// fixed-order FP64 reductions, boundary ghosts, TMA tile loads, the
+// Lax-Wendroff neighbour terms and the watchdog / audit epilogue.
+#pragma once
+
+#include <cuda.h>  // CUtensorMap (the encoder is fetched at run time; libcuda is not linked)
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+#include "d2v16.cuh"
+
+namespace lbmk {
+
+using namespace d2v16;
+
+constexpr unsigned long long NONE = ~0ull;
+// Thread-block shapes: FP32 32 x 8 (memory-bound, more warps in flight),
+// FP64 32 x 4 (FP64-ALU-bound; smaller blocks balance the SMs better).
+template <typename R> struct Shape;
+template <> struct Shape<float> { static constexpr int X = 32, Y = 8, MINB = 4; };
+template <> struct Shape<double> { static constexpr int X = 32, Y = 4, MINB = 4; };
+constexpr int AUX_X = 32, AUX_Y = 8, AUX_N = AUX_X * AUX_Y;  // init / moments / audit
+
+// Device-resident status block of one context.
+struct DevStatus {
+  unsigned long long blocks_done; // step blocks finished; time level = blocks_done / nblocks
+  unsigned int arrive_audit;      // blocks finished in a standalone audit
+  unsigned int pad;
+  unsigned long long first_bad;   // first level with non-finite / rho <= 0
+  unsigned long long first_negT;  // first level with T <= 0
+  unsigned long long audit_count; // fused audits written so far
+  int tma_timeout;                // a tile load did not complete in time
+  int pad2;
+  double audit_now[4];            // result of the standalone audit
+  double audit_totals[LBM_AUDIT_RING][4];
+  long long audit_steps[LBM_AUDIT_RING];
+};
+
+template <typename R>
+struct StepArgs {
+  Coeffs<R> K;
+  int nx, ny;
+  long long pitch, plane;
+  int bc[4];          // x-, x+, y-, y+
+  R wall[4][3];       // (u, v, T) of LBM_BC_WALL sides
+  const R* geq;       // [4][16] Dirichlet ghost populations
+  DevStatus* st;
+  double* partial;    // [nblocks][4] audit scratch
+  int audit_every;
+  int nblocks;
+  double area;        // dx * dy
+};
+
+// ---------------------------------------------------------------------------
+// Fixed-order FP64 reductions of four sums (bitwise reproducible)
+// ---------------------------------------------------------------------------
+// Warp sum of v[0..3] by a transposing butterfly: the first two exchange
+// levels halve the number of live sums, so a lane does 6 additions instead of
+// 20. Afterwards lanes 0, 8, 16, 24 hold the warp totals of sums 0, 1, 2, 3.
+__device__ __forceinline__ double warp_sum4(const double v[4], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const double s0 = h16 ? v[0] : v[2], s1 = h16 ? v[1] : v[3];
+  double k0 = (h16 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, s0, 16);
+  double k1 = (h16 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, s1, 16);
+  double k = (h8 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
+// Block sum of v[0..3] (N threads); threads 0..3 return sums 0..3.
+template <int N>
+__device__ __forceinline__ double block_sum4(const double v[4], double (*sm)[4]) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const double k = warp_sum4(v, lane);
+  if ((lane & 7) == 0) sm[warp][lane >> 3] = k;
+  __syncthreads();
+  double s = 0.0;
+  if (t < 4)
+    for (int w = 0; w < N / 32; ++w) s += sm[w][t];
+  return s;
+}
+
+// Sum of partial[b][q] over b by all N threads of one block, in a fixed
+// order: thread t takes q = t % 4 and blocks b = t/4, t/4 + N/4, ...; then a
+// fixed tree. Threads 0..3 return the totals of q = 0..3.
+template <int N>
+__device__ __forceinline__ double final_sum4(const double* partial, int nblocks,
+                                             double (*sm)[4]) {
+  constexpr int G = N / 4;
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int q = t & 3, j = t >> 2;
+  double s = 0.0;
+#pragma unroll 4
+  for (int b = j; b < nblocks; b += G) s += __ldcg(partial + 4 * b + q);
+  sm[j][q] = s;
+  __syncthreads();
+#pragma unroll
+  for (int stride = G / 2; stride > 0; stride >>= 1) {
+    if (j < stride) sm[j][q] += sm[j + stride][q];
+    __syncthreads();
+  }
+  return t < 4 ? sm[0][t] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Boundary ghosts
+// ---------------------------------------------------------------------------
+template <typename R, typename Off>
+__device__ __forceinline__ Cons<R> load_cons(const Coeffs<R>& K, const R* __restrict__ fin,
+                                             Off plane, Off idx) {
+  R f[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) f[i] = fin[i * plane + idx];
+  Groups<R> d;
+  transform(f, d);
+  return conserved(K, d);
+}
+
+// Ghost populations outside `side` of the node with conserved moments `own`.
+// `inward` is the index of the next node inwards (EXTRAP), `has_inward`
+// false when the grid is one node deep in that direction.
+template <typename R, typename Off>
+__device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict__ fin,
+                                      Off plane, int side, Cons<R> own, Off inward,
+                                      bool has_inward, R g[16]) {
+  const int kind = A.bc[side];
+  if (kind == LBM_BC_EQ) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) g[i] = A.geq[side * 16 + i];
+    return;
+  }
+  Cons<R> s = own;
+  if (kind == LBM_BC_REFLECT) {
+    if (side < 2) s.jx = -s.jx; else s.jy = -s.jy;
+  } else if (kind == LBM_BC_WALL) {
+    const R u = A.wall[side][0], v = A.wall[side][1], T = A.wall[side][2];
+    s.jx = own.rho * u;
+    s.jy = own.rho * v;
+    s.e = own.rho * T + R(0.5) * own.rho * (u * u + v * v);
+  } else {  // LBM_BC_EXTRAP
+    const Cons<R> in = has_inward ? load_cons(A.K, fin, plane, inward) : own;
+    const R r1 = recip(own.rho), r2 = recip(in.rho);
+    const R u1 = own.jx * r1, v1 = own.jy * r1, u2 = in.jx * r2, v2 = in.jy * r2;
+    const R T1 = own.e * r1 - R(0.5) * (u1 * u1 + v1 * v1);
+    const R T2 = in.e * r2 - R(0.5) * (u2 * u2 + v2 * v2);
+    R rho = R(2) * own.rho - in.rho, u = R(2) * u1 - u2, v = R(2) * v1 - v2,
+      T = R(2) * T1 - T2;
+    if (!(rho > R(0) && T > R(0))) {
+      rho = own.rho; u = u1; v = v1; T = T1;
+    }
+    s.rho = rho;
+    s.jx = rho * u;
+    s.jy = rho * v;
+    s.e = rho * T + R(0.5) * rho * (u * u + v * v);
+  }
+  feq(A.K, s.rho, s.jx, s.jy, s.e, g);
+}
+
+// ---------------------------------------------------------------------------
+// Tile loads: TMA (cp.async.bulk.tensor) into shared memory, mbarrier-tracked
+// ---------------------------------------------------------------------------
+// The populations are a 3D tensor (x: pitch, y: ny, i: 16). A block's tile is
+// its BX x BY nodes plus a halo: rows y0-1 .. y0+BY, columns x0-4 .. x0+BX+3
+// (4 columns instead of 1 so that the box starts on a 16-byte boundary), all
+// 16 populations, landing in shared memory as [16][BY+2][BX+8]. Boxes that
+// reach outside the tensor are filled with zeros; those values are never
+// used (boundary nodes take ghosts, periodic wraps read global memory).
+constexpr int HALO_X = 4;
+template <typename R>
+struct Tile {
+  static constexpr int BXP = Shape<R>::X + 2 * HALO_X;
+  static constexpr int ROWS = Shape<R>::Y + 2;
+  static constexpr int ELEMS = 16 * ROWS * BXP;
+  static constexpr unsigned BYTES = ELEMS * sizeof(R);
+};
+constexpr long long TMA_WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the barrier for at most `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  long long limit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > limit) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map, int x, int y,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(0), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Lax-Wendroff neighbour terms (Eq. A.1b) with boundary ghosts
+// ---------------------------------------------------------------------------
+// acc[i] += aW f(x-dx) + aE f(x+dx) + aS f(y-dy) + aN f(y+dy) for the node at
+// tile pointer `ctr` (population i at ctr[i * PS], rows BXP apart). Interior
+// nodes read the tile only; edge nodes wrap (periodic, global memory) or use
+// the ghost populations of their side.
+template <typename R, typename Off, int BXP>
+__device__ __forceinline__ void neighbour_terms(const StepArgs<R>& A, const R* __restrict__ fin,
+                                                const R* ctr, int PS, Off P, Off pitch, Off c,
+                                                int x, int y, const Cons<R>& m, R (&acc)[16]) {
+  if (x > 0 && x < A.nx - 1 && y > 0 && y < A.ny - 1) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      R a = acc[i];
+      if (has_x(i)) {
+        a += A.K.aW[i] * ctr[i * PS - 1];
+        a += A.K.aE[i] * ctr[i * PS + 1];
+      }
+      if (has_y(i)) {
+        a += A.K.aS[i] * ctr[i * PS - BXP];
+        a += A.K.aN[i] * ctr[i * PS + BXP];
+      }
+      acc[i] = a;
+    }
+    return;
+  }
+  // x- neighbour (west)
+  if (x > 0) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_x(i)) acc[i] += A.K.aW[i] * ctr[i * PS - 1];
+  } else if (A.bc[0] == LBM_BC_PERIODIC) {
+    const Off n = c + (Off)(A.nx - 1);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_x(i)) acc[i] += A.K.aW[i] * fin[i * P + n];
+  } else {
+    R g[16];
+    ghost(A, fin, P, 0, m, c + 1, A.nx > 1, g);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_x(i)) acc[i] += A.K.aW[i] * g[i];
+  }
+  // x+ neighbour (east)
+  if (x < A.nx - 1) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_x(i)) acc[i] += A.K.aE[i] * ctr[i * PS + 1];
+  } else if (A.bc[1] == LBM_BC_PERIODIC) {
+    const Off n = c - (Off)(A.nx - 1);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_x(i)) acc[i] += A.K.aE[i] * fin[i * P + n];
+  } else {
+    R g[16];
+    ghost(A, fin, P, 1, m, c - 1, A.nx > 1, g);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_x(i)) acc[i] += A.K.aE[i] * g[i];
+  }
+  // y- neighbour (south)
+  if (y > 0) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_y(i)) acc[i] += A.K.aS[i] * ctr[i * PS - BXP];
+  } else if (A.bc[2] == LBM_BC_PERIODIC) {
+    const Off n = c + (Off)(A.ny - 1) * pitch;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_y(i)) acc[i] += A.K.aS[i] * fin[i * P + n];
+  } else {
+    R g[16];
+    ghost(A, fin, P, 2, m, c + pitch, A.ny > 1, g);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_y(i)) acc[i] += A.K.aS[i] * g[i];
+  }
+  // y+ neighbour (north)
+  if (y < A.ny - 1) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_y(i)) acc[i] += A.K.aN[i] * ctr[i * PS + BXP];
+  } else if (A.bc[3] == LBM_BC_PERIODIC) {
+    const Off n = c - (Off)(A.ny - 1) * pitch;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_y(i)) acc[i] += A.K.aN[i] * fin[i * P + n];
+  } else {
+    R g[16];
+    ghost(A, fin, P, 3, m, c - pitch, A.ny > 1, g);
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (has_y(i)) acc[i] += A.K.aN[i] * g[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Watchdog and audit epilogue of a step block (N threads)
+// ---------------------------------------------------------------------------
+// Records bad / T <= 0 nodes (one atomic per warp), counts the block as done
+// and, on audit steps, writes the block's FP64 partial sums of (rho, j, e);
+// the last block to finish reduces all partials in a fixed order into the
+// audit ring. `cons` is zero for inactive threads.
+template <int N, typename R>
+__device__ __forceinline__ void step_epilogue(const StepArgs<R>& A, unsigned long long step,
+                                              bool audit, bool bad, bool negT,
+                                              const R (&cons)[4], double (*sm)[4], int* s_last) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const unsigned badm = __ballot_sync(0xffffffffu, bad);
+  const unsigned negm = __ballot_sync(0xffffffffu, negT);
+  if ((t & 31) == 0) {
+    if (badm) atomicMin(&A.st->first_bad, step);
+    if (negm) atomicMin(&A.st->first_negT, step);
+  }
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (!audit) {
+    if (t == 0) atomicAdd(&A.st->blocks_done, 1ull);
+    return;
+  }
+  const double tot[4] = {(double)cons[0], (double)cons[1], (double)cons[2], (double)cons[3]};
+  const double bs = block_sum4<N>(tot, sm);
+  if (t < 4) A.partial[4 * bid + t] = bs;
+  __syncthreads();
+  if (t == 0) {
+    __threadfence();
+    const unsigned long long prev = atomicAdd(&A.st->blocks_done, 1ull);
+    *s_last = (prev + 1 == (step + 1) * (unsigned long long)A.nblocks);
+  }
+  __syncthreads();
+  if (*s_last) {
+    __threadfence();
+    const double tot4 = final_sum4<N>(A.partial, A.nblocks, sm);
+    if (t < 4) {
+      const unsigned long long slot = A.st->audit_count % LBM_AUDIT_RING;
+      A.st->audit_totals[slot][t] = tot4 * A.area;
+    }
+    __syncthreads();
+    if (t == 0) {
+      const unsigned long long slot = A.st->audit_count % LBM_AUDIT_RING;
+      A.st->audit_steps[slot] = (long long)step;
+      A.st->audit_count += 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core step (lbm_tc.cu)
+// ---------------------------------------------------------------------------
+constexpr int TC_X = 32, TC_Y = 4;  // nodes per CTA: 32 x 4 = 128
+// TF32 high/low parts of M and M^-1 in the layout the kernel stages (4 x 1 KB).
+void tc_prepare_constants(const double (&M)[16][16], const double (&Minv)[16][16],
+                          unsigned char (&out)[4][1024]);
+cudaError_t tc_launch(const CUtensorMap& tm, const float* fin, float* fout,
+                      const StepArgs<float>& A, const unsigned char* bconst, const float* wk,
+                      dim3 grid, cudaStream_t s);
+
+}  // namespace lbmk
