@@ -15,10 +15,18 @@ L2 and no dirty lines left to write back. Each timed step
 is bracketed by CUDA events on the launching stream; the GPU is kept busy
 while the host enqueues the loop, so host launch latency is not timed.
 
+Each context's launch shape is chosen first with lbm_autotune (a timing of
+the candidate block counts that leaves the state untouched).
+
 Lines printed (rank 0): one JSON object. ``value`` is FP32-path cell-updates/s
 summed over ranks; ``fp64`` carries the FP64 path measured the same way;
-``cpu_baseline`` is the FP64 numpy oracle on one host core over a bounded
-sample; ``e2e`` times the same step through the C ABI with host buffers.
+``large_grid`` the FP32 and tensor-core (3xTF32) steps on the 2048 x 1024
+shock-bubble grid (268 MB per step, larger than L2, so timed as CUDA-graph
+replays back to back) with their errors against an FP64 GPU run;
+``tubes`` the batched quasi-1D Riemann problems; ``cpu_baseline`` is the FP64
+numpy oracle on one host core over a bounded sample; ``e2e`` times the same
+step through the C ABI with host buffers; ``clocks`` are nvidia-smi samples
+taken inside the FP32 timed region (and over the whole run).
 
 ``--impl reference`` times the CPU oracle instead (the only reference
 implementation this method has), on the same workload, rank 0 only.
@@ -118,41 +126,55 @@ def cpu_baseline(seconds):
 # GPU measurement
 # ----------------------------------------------------------------------------
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi every 200 ms."""
+    """Samples SM clocks and throttle reasons with nvidia-smi every 100 ms from
+    a reader thread that stamps each sample with the host clock, so that the
+    samples taken inside a timed region can be picked out afterwards."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, device_uuid=None):
-        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        import threading
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "100"]
         if device_uuid:
             cmd += ["-i", device_uuid]
+        self.samples = []          # (host time, sm MHz, max MHz, reasons)
         try:
             self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < 5.0:   # running before timing starts
+            time.sleep(0.02)
 
-    def stop(self):
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.p.terminate()
-        out, _ = self.p.communicate(timeout=10)
-        sm, mx, reasons = [], None, set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in out.strip().splitlines():
+    def _read(self):
+        for line in self.p.stdout:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
+                sm, mx = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
-            for name, val in zip(names, parts[5:9]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "samples": len(sm), "reasons": sorted(reasons)}
+            reasons = {n for n, v in zip(self.NAMES, parts[5:9]) if v.lower() == "active"}
+            self.samples.append((time.perf_counter(), sm, mx, reasons))
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            self.t.join(timeout=5)
+
+    def summary(self, t0=None, t1=None):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sel = [x for x in self.samples if (t0 is None or x[0] >= t0) and (t1 is None or x[0] <= t1)]
+        return {"sm_mhz": statistics.median(x[1] for x in sel) if sel else None,
+                "sm_max_mhz": sel[-1][2] if sel else None, "samples": len(sel),
+                "reasons": sorted(set().union(*[x[3] for x in sel])) if sel else []}
 
 
 def device_uuid(torch):
@@ -181,10 +203,78 @@ def time_steps(torch, lbm, ctx, stream, flush, K, W):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def make_ctx(lbm, w, precision, audit_every, stream):
+def time_graph_steps(torch, lbm, ctx, stream, n, reps):
+    """Mean ms per step of `reps` timed calls of lbm_step(ctx, n) (n a
+    multiple of 64: CUDA-graph replays back to back), after one warm-up call.
+    Consecutive steps are not flushed: a grid smaller than L2 stays there."""
+    with torch.cuda.stream(stream):
+        lbm.lbm_step(ctx, n)
+        stream.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            lbm.lbm_step(ctx, n)
+            b.record(stream)
+        stream.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / (reps * n)
+
+
+def field_error(lbm, ctx, ref):
+    """Relative L-infinity error per field of ctx's moments against `ref`
+    (rho and T relative to their maxima, u and v to the maximum speed)."""
+    m = [np.empty_like(ref[0]) for _ in range(4)]
+    lbm.lbm_moments(ctx, *m)
+    speed = np.sqrt(ref[1] ** 2 + ref[2] ** 2).max()
+    return {"rho": float(np.abs(m[0] - ref[0]).max() / np.abs(ref[0]).max()),
+            "u": float(np.abs(m[1] - ref[1]).max() / speed),
+            "v": float(np.abs(m[2] - ref[2]).max() / speed),
+            "T": float(np.abs(m[3] - ref[3]).max() / np.abs(ref[3]).max())}
+
+
+def bubble_measure(torch, lbm, stream, audit_every, hbm_peak):
+    """The 2048 x 1024 shock-bubble grid (268 MB of FP32 traffic per step,
+    larger than L2): FP32 and tensor-core (3xTF32) steps timed as back-to-back
+    graph replays, and both compared with an FP64 GPU run after the same
+    number of steps."""
+    import workloads
+    wl = workloads.shock_bubble()
+    cl = wl.nx * wl.ny
+    out = {"workload": "shock_bubble_%dx%d" % (wl.nx, wl.ny), "unit": UNIT,
+           "timing": "64-step CUDA-graph replays back to back (inputs larger than L2)"}
+    nsteps = 256
+    c64 = make_ctx(lbm, wl, "fp64", 0, stream)
+    lbm.lbm_step(c64, nsteps)
+    ref = [np.empty((wl.ny, wl.nx)) for _ in range(4)]
+    lbm.lbm_moments(c64, *ref)
+    lbm.lbm_destroy(c64)
+    for prec, key in (("fp32", "fp32"), ("tc_tf32x3", "tensor_core_tf32x3")):
+        ctx = make_ctx(lbm, wl, prec, 0, stream)
+        try:
+            lbm.lbm_step(ctx, nsteps)
+            err = field_error(lbm, ctx, ref)
+            st = lbm.lbm_status(ctx)
+            ctx2 = make_ctx(lbm, wl, prec, audit_every, stream)
+            try:
+                ms = time_graph_steps(torch, lbm, ctx2, stream, 64, 10)
+                blocks = lbm.lbm_step_blocks(ctx2)
+            finally:
+                lbm.lbm_destroy(ctx2)
+        finally:
+            lbm.lbm_destroy(ctx)
+        gbs = BYTES_PER_CELL["fp32"] * cl / (ms * 1e-3) / 1e9
+        out[key] = {"value": cl / (ms * 1e-3), "ms_per_step": ms, "achieved_gbs": gbs,
+                    "frac_of_hbm": gbs / hbm_peak, "step_blocks": blocks,
+                    "error_vs_fp64_gpu_after_%d_steps" % nsteps: err, "status": list(st)}
+    return out
+
+
+def make_ctx(lbm, w, precision, audit_every, stream, tune=True):
     cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, precision, audit_every)
     ctx = lbm.lbm_create(cfg, stream)
     lbm.lbm_set_init(ctx, *[np.ascontiguousarray(a) for a in w.fields()])
+    if tune:
+        lbm.lbm_autotune(ctx, 20)
     return ctx
 
 
@@ -286,8 +376,12 @@ def run_ours(args):
     cells = w.nx * w.ny
     stream = torch.cuda.Stream()
     flush = L2Flush(torch)
-    ctx32 = make_ctx(lbm, w, "fp32", args.audit_every, stream)
-    ctx64 = make_ctx(lbm, w, "fp64", args.audit_every, stream)
+    clocks = Clocks(device_uuid(torch))
+    # The timed per-step runs use the library's default launch (one block per
+    # tile): lbm_autotune times steps back to back with a warm L2, the regime
+    # of a long run (reported below as "sustained"), not flushed single steps.
+    ctx32 = make_ctx(lbm, w, "fp32", args.audit_every, stream, tune=False)
+    ctx64 = make_ctx(lbm, w, "fp64", args.audit_every, stream, tune=False)
     K, W = args.steps, args.warmup
 
     # FP64 path (not the headline; measured first, same procedure)
@@ -297,12 +391,13 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(device_uuid(torch))
+    h0 = time.perf_counter()
     t32 = time_steps(torch, lbm, ctx32, stream, flush, K, W)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    h1 = time.perf_counter()
     if dist:
         dist.barrier()
+    blocks32, blocks64 = lbm.lbm_step_blocks(ctx32), lbm.lbm_step_blocks(ctx64)
     total32 = sum(t32)
     total64 = sum(t64)
     if dist:
@@ -327,22 +422,34 @@ def run_ours(args):
     lbm.lbm_destroy(ctx32)
     lbm.lbm_destroy(ctx64)
 
-    # Same FP32 step on a grid larger than L2 (the 2048 x 1024 shock-bubble
-    # set-up, 268 MB of traffic per step): the HBM-bound regime.
-    large = None
-    if not args.no_large:
-        import workloads
-        wl = workloads.shock_bubble()
-        ctxl = make_ctx(lbm, wl, "fp32", args.audit_every, stream)
-        tl = time_steps(torch, lbm, ctxl, stream, flush, min(K, 50), W)
-        lbm.lbm_destroy(ctxl)
-        msl = sum(tl) / len(tl)
-        cl = wl.nx * wl.ny
-        gbl = BYTES_PER_CELL["fp32"] * cl / (msl * 1e-3) / 1e9
-        large = {"workload": "shock_bubble_%dx%d" % (wl.nx, wl.ny), "value": cl / (msl * 1e-3),
-                 "unit": UNIT, "ms_per_step": msl, "achieved_gbs": gbl, "steps": len(tl)}
+    # The same grid in a long run: autotuned launch shape, 64-step CUDA-graph
+    # replays back to back, no flush (the 15 MB grid stays in L2 between
+    # consecutive steps, as it does in a real run of this size).
+    sustained = {}
+    for prec in ("fp32", "fp64"):
+        ctx = make_ctx(lbm, w, prec, args.audit_every, stream)
+        try:
+            ms = time_graph_steps(torch, lbm, ctx, stream, 640, 5)
+            sustained[prec] = {"value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                               "step_blocks": lbm.lbm_step_blocks(ctx)}
+        finally:
+            lbm.lbm_destroy(ctx)
+    sustained["timing"] = ("autotuned launch, 640 steps per timed call as CUDA-graph replays "
+                           "back to back, L2 not flushed (grid resident in L2)")
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    # FP32 and tensor-core steps on a grid larger than L2 (the 2048 x 1024
+    # shock-bubble set-up): the HBM-bound regime, errors against FP64.
+    large = None if args.no_large else bubble_measure(torch, lbm, stream, args.audit_every, hbm_peak)
 
     tubes = None if args.no_tubes else tubes_measure(torch, lbm, stream, args)
+    clocks.stop()
 
     if rank != 0:
         if dist:
@@ -351,14 +458,6 @@ def run_ours(args):
     ms32 = total32 / K
     ms64 = total64 / K
     gbs = BYTES_PER_CELL["fp32"] * cells / (ms32 * 1e-3) / 1e9
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    if large:
-        large["frac_of_hbm"] = large["achieved_gbs"] / hbm_peak
     if tubes:
         tubes["frac_of_hbm"] = tubes["achieved_gbs"] / hbm_peak
     tflops64 = FLOPS_PER_CELL * cells / (ms64 * 1e-3) / 1e12
@@ -375,7 +474,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": config_json(w, "fp32", args.audit_every),
+        "config": dict(config_json(w, "fp32", args.audit_every), step_blocks=blocks32),
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": gbs / hbm_peak, "traffic": traffic_record("k_step<float>"),
                      "kernel": "k_step<float>",
@@ -383,7 +482,7 @@ def run_ours(args):
                      "bytes_per_cell_update": BYTES_PER_CELL["fp32"]},
         "accuracy_fp32_vs_fp64": acc,
         "fp64": {"value": world * cells * K / (total64 * 1e-3), "unit": UNIT,
-                 "ms_per_step": ms64, "dtype": "f64",
+                 "ms_per_step": ms64, "dtype": "f64", "step_blocks": blocks64,
                  "roofline": {"bound": "alu", "achieved": tflops64, "peak": FP64_PEAK_TFLOPS,
                               "unit": "TFLOP/s", "frac": tflops64 / FP64_PEAK_TFLOPS,
                               "peak_source": "nominal FP64 rate (2 DFMA/clk/SM)",
@@ -391,12 +490,13 @@ def run_ours(args):
                               "traffic": traffic_record("k_step<double>"),
                               "hbm_frac": BYTES_PER_CELL["fp64"] * cells / (ms64 * 1e-3) / 1e9 / hbm_peak}},
         "status": {"fp32": list(s32), "fp64": list(s64)},
-        "fp32_large_grid": large,
+        "sustained": sustained,
+        "large_grid": large,
         "tubes": tubes,
         "e2e": {"value": cells / statistics.mean(e2e_t), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "lbm_set_populations(pinned host) + lbm_step(1) + lbm_moments(pinned host)"},
-        "clocks": clk,
+        "clocks": dict(clocks.summary(h0, h1), whole_run=clocks.summary()),
         "gpu_launches": K,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -432,7 +532,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--audit-every", type=int, default=10)

@@ -165,6 +165,26 @@ int lbm_set_populations(lbm_ctx* ctx, const void* f, long long step, int on_devi
 /* Bytes per population element (8 or 4) of ctx. */
 int lbm_element_size(lbm_ctx* ctx);
 
+/* Launch shape of the step (LBM_FP64 / LBM_FP32). A step is one persistent
+ * launch of `blocks` thread blocks that share the grid's node tiles (32 x 8
+ * nodes in FP32, 32 x 4 in FP64) through a device-side counter. Results do
+ * not depend on it (each node's update is the same, audit partials are kept
+ * per tile); only the speed does.
+ *  lbm_set_step_blocks: 0 = the default (as many blocks as fit on the
+ *    device at once, at most one per tile); larger values are capped at the
+ *    number of tiles. Synchronises; LBM_ERR_UNSUPPORTED for LBM_TC_TF32X3
+ *    (one CTA per 128-node tile).
+ *  lbm_step_blocks: the current value (-1 for a NULL ctx).
+ *  lbm_autotune: times `launches` step launches for each of 1, 2, ... blocks
+ *    per multiprocessor and keeps the fastest. The timed launches read the
+ *    current populations and write the spare buffer against scratch
+ *    counters: the state, the step count, the watchdog and the audit log are
+ *    unchanged. Call it after lbm_set_init / lbm_set_populations.
+ *    Synchronises; a no-op for LBM_TC_TF32X3. */
+int lbm_set_step_blocks(lbm_ctx* ctx, int blocks);
+int lbm_step_blocks(lbm_ctx* ctx);
+int lbm_autotune(lbm_ctx* ctx, int launches);
+
 /* One-line description of the last error on ctx (or of the last lbm_create
  * failure on this thread when ctx is NULL). Never NULL. */
 const char* lbm_last_error(lbm_ctx* ctx);

@@ -40,56 +40,46 @@ constexpr int GRAPH_CHUNK = 64;  // steps per captured graph (even)
 // ---------------------------------------------------------------------------
 // The fused step
 // ---------------------------------------------------------------------------
+// A step launch covers the grid's node tiles of Shape<R>::X x Shape<R>::Y
+// nodes, one thread per node, each tile and its halo copied into shared
+// memory by one TMA. Two launch forms, chosen per grid by lbm_autotune:
+//  k_step       one tile per block (grid = all tiles); the copy of a tile
+//               overlaps other blocks' compute through the hardware's block
+//               scheduling. Best for grids that fit on the device in about
+//               one wave.
+//  k_step_pipe  persistent: nblocks < ntiles blocks, block b takes tiles b,
+//               b + nblocks, ... and copies its next tile into a second
+//               shared-memory stage while it computes the current one.
+// Which block computes which tile changes no result: each node's update is
+// the same, and audit partials are kept per tile.
 // Off: unsigned (32-bit element offsets, grids with 16 * plane < 2^32) or
-// long long. One thread per node; the block's tile and halo come in by one
-// TMA copy, the stencil reads shared memory.
+// long long.
+template <typename R>
+__device__ __forceinline__ void load_tile(R* stage, const CUtensorMap* tmap, unsigned long long* bar,
+                                          int tile, int tiles_x) {
+  const int x0 = (tile % tiles_x) * Shape<R>::X, y0 = (tile / tiles_x) * Shape<R>::Y;
+  mbar_expect_tx(bar, Tile<R>::BYTES);
+  tma_load_tile(stage, tmap, x0 - HALO_X, y0 - 1, bar);
+}
+
+// Updates the nodes of tile `cur` from its copy in shared memory `stage`:
+// group transforms, conserved moments, Eq. 14 equilibria, relaxation and
+// back-map, f (1 - cx^2 - cy^2) + collision + Lax-Wendroff neighbour terms,
+// store. Accumulates the watchdog flags; on audit steps writes the tile's
+// partial sums (a block-wide reduction: every thread of the block calls it).
 template <typename R, typename Off>
-__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
-    k_step(const __grid_constant__ CUtensorMap tmap, const R* __restrict__ fin,
-           R* __restrict__ fout, const StepArgs<R> A) {
+__device__ __forceinline__ void step_tile(const StepArgs<R>& A, const R* __restrict__ fin,
+                                          R* __restrict__ fout, const R* stage, int cur, bool audit,
+                                          double (*sm)[4], bool& bad, bool& negT) {
   constexpr int BXD = Shape<R>::X, BYD = Shape<R>::Y, N = BXD * BYD;
-  constexpr int BXP = Tile<R>::BXP, ROWS = Tile<R>::ROWS;
-  __shared__ __align__(128) R tile[Tile<R>::ELEMS];
-  __shared__ double sm[N / 4][4];
-  __shared__ unsigned long long bar;
-  __shared__ unsigned long long s_step;
-  __shared__ int s_audit, s_last;
-  const int t = threadIdx.y * BXD + threadIdx.x;
-  const int x0 = blockIdx.x * BXD, y0 = blockIdx.y * BYD;
-  if (t == 0) {
-    // Start the tile copy first so that its latency overlaps the read of
-    // the step counter.
-    mbar_init(&bar, 1);
-    mbar_expect_tx(&bar, Tile<R>::BYTES);
-    tma_load_tile(tile, &tmap, x0 - HALO_X, y0 - 1, &bar);
-    const unsigned long long done = *(volatile unsigned long long*)&A.st->blocks_done;
-    const unsigned long long step = done / (unsigned long long)A.nblocks;
-    s_step = step;
-    s_audit = A.audit_every > 0 && (step % (unsigned long long)A.audit_every) == 0;
-  }
-  __syncthreads();
-  const unsigned long long step = s_step;
-  const bool audit = s_audit != 0;
-  // Every thread waits for the tile (bounded); the block decides together.
-  if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, TMA_WAIT_CYCLES))) {
-    // The copy did not land: record it, give it a second bounded wait so that
-    // no copy is left writing into shared memory, and leave without output.
-    if (t == 0) atomicExch(&A.st->tma_timeout, 1);
-    mbar_wait_bounded(&bar, 0, TMA_WAIT_CYCLES);
-    return;
-  }
-
-  const int x = x0 + threadIdx.x;
-  const int y = y0 + threadIdx.y;
-  const bool active = x < A.nx && y < A.ny;
-  R cons[4] = {R(0), R(0), R(0), R(0)};  // widened to FP64 on audit steps only
-  bool bad = false, negT = false;
-
-  if (active) {
+  constexpr int BXP = Tile<R>::BXP, PS = Tile<R>::ROWS * BXP;
+  const int x = (cur % A.tiles_x) * BXD + threadIdx.x;
+  const int y = (cur / A.tiles_x) * BYD + threadIdx.y;
+  R mc[4] = {R(0), R(0), R(0), R(0)};  // conserved moments, widened on audit steps
+  if (x < A.nx && y < A.ny) {
     const Off P = (Off)A.plane, pitch = (Off)A.pitch;
     const Off c = (Off)y * pitch + (Off)x;
-    const R* ctr = tile + (threadIdx.y + 1) * BXP + threadIdx.x + HALO_X;  // + i * ROWS * BXP
-    constexpr int PS = ROWS * BXP;
+    const R* ctr = stage + (threadIdx.y + 1) * BXP + threadIdx.x + HALO_X;
     R f[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) f[i] = ctr[i * PS];
@@ -101,16 +91,112 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
 #pragma unroll
     for (int i = 0; i < 16; ++i) acc[i] = A.K.a0[i] * f[i] + acc[i];
 
-    bad = !(m.rho > R(0)) || !isfinite(m.rho + m.jx + m.jy + m.e);
-    negT = !bad && !(press > R(0));
-    cons[0] = m.rho; cons[1] = m.jx; cons[2] = m.jy; cons[3] = m.e;
-
+    const bool b = !(m.rho > R(0)) || !isfinite(m.rho + m.jx + m.jy + m.e);
+    bad |= b;
+    negT |= !b && !(press > R(0));
+    mc[0] = m.rho; mc[1] = m.jx; mc[2] = m.jy; mc[3] = m.e;
     neighbour_terms<R, Off, BXP>(A, fin, ctr, PS, P, pitch, c, x, y, m, acc);
 #pragma unroll
     for (int i = 0; i < 16; ++i) fout[i * P + c] = acc[i];
   }
+  if (audit) {  // FP64 only on audit steps
+    const double tot[4] = {(double)mc[0], (double)mc[1], (double)mc[2], (double)mc[3]};
+    audit_tile<N>(A, cur, tot, sm);
+  }
+}
 
-  step_epilogue<N>(A, step, audit, bad, negT, cons, sm, &s_last);
+template <typename R, typename Off>
+__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
+    k_step(const __grid_constant__ CUtensorMap tmap, const R* __restrict__ fin,
+           R* __restrict__ fout, const StepArgs<R> A) {
+  constexpr int N = Shape<R>::X * Shape<R>::Y;
+  __shared__ __align__(128) R tile[Tile<R>::ELEMS];
+  __shared__ double sm[N / 4][4];
+  __shared__ unsigned long long bar;
+  __shared__ unsigned long long s_step;
+  __shared__ int s_audit, s_last;
+  const int t = threadIdx.y * Shape<R>::X + threadIdx.x;
+  if (t == 0) {
+    // Start the tile copy first so that its latency overlaps the read of
+    // the step counter.
+    mbar_init(&bar, 1);
+    load_tile(tile, &tmap, &bar, blockIdx.x, A.tiles_x);
+    s_step = read_step(A, &s_audit);
+  }
+  __syncthreads();
+  const bool audit = s_audit != 0;
+  // Every thread waits for the tile (bounded); the block decides together.
+  if (!__syncthreads_and(mbar_wait_bounded(&bar, 0, TMA_WAIT_CYCLES))) {
+    // The copy did not land: record it, give it a second bounded wait so that
+    // no copy is left writing into shared memory, and leave without output.
+    if (t == 0) {
+      atomicExch(&A.st->tma_timeout, 1);
+      mbar_wait_bounded(&bar, 0, TMA_WAIT_CYCLES);
+      audit_ticket_on_exit(A, audit);
+    }
+    return;
+  }
+  bool bad = false, negT = false;
+  step_tile<R, Off>(A, fin, fout, tile, blockIdx.x, audit, sm, bad, negT);
+  const unsigned long long step = s_step;
+  watchdog_flags(A.st, step, bad, negT);
+  if (audit) audit_finish<N>(A, step, sm, &s_last);
+}
+
+// Two tile stages (each a multiple of 128 bytes) plus room to align the first
+// to 128 bytes, as TMA destinations require.
+template <typename R>
+constexpr size_t pipe_smem_bytes() { return 2 * sizeof(R) * (size_t)Tile<R>::ELEMS + 128; }
+static_assert(sizeof(float) * Tile<float>::ELEMS % 128 == 0, "stage size");
+static_assert(sizeof(double) * Tile<double>::ELEMS % 128 == 0, "stage size");
+
+template <typename R, typename Off>
+__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB_PIPE)
+    k_step_pipe(const __grid_constant__ CUtensorMap tmap, const R* __restrict__ fin,
+                R* __restrict__ fout, const StepArgs<R> A) {
+  constexpr int N = Shape<R>::X * Shape<R>::Y;
+  extern __shared__ __align__(128) unsigned char pipe_smem[];
+  R* const stages = reinterpret_cast<R*>(  // [2][Tile<R>::ELEMS], 128-byte aligned
+      pipe_smem + ((128u - (smem_addr(pipe_smem) & 127u)) & 127u));
+  __shared__ double sm[N / 4][4];
+  __shared__ unsigned long long bar[2];
+  __shared__ unsigned long long s_step;
+  __shared__ int s_audit, s_last;
+  const int t = threadIdx.y * Shape<R>::X + threadIdx.x;
+  const int G = (int)gridDim.x;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    load_tile(stages, &tmap, &bar[0], blockIdx.x, A.tiles_x);  // nblocks <= ntiles
+    s_step = read_step(A, &s_audit);
+  }
+  __syncthreads();
+  bool bad = false, negT = false;
+  int k = 0;
+  for (int cur = blockIdx.x; cur < A.ntiles; cur += G, ++k) {
+    const int s = k & 1;
+    const bool more = cur + G < A.ntiles;
+    // Stage 1 - s was released at the end of the previous tile.
+    if (t == 0 && more)
+      load_tile(stages + (1 - s) * Tile<R>::ELEMS, &tmap, &bar[1 - s], cur + G, A.tiles_x);
+    // Every thread waits for the tile (bounded); the block decides together.
+    if (!__syncthreads_and(mbar_wait_bounded(&bar[s], (k >> 1) & 1, TMA_WAIT_CYCLES))) {
+      // A copy did not land: record it, give the copies issued a second
+      // bounded wait so that none is left writing into shared memory, leave.
+      if (t == 0) {
+        atomicExch(&A.st->tma_timeout, 1);
+        mbar_wait_bounded(&bar[s], (k >> 1) & 1, TMA_WAIT_CYCLES);
+        if (more) mbar_wait_bounded(&bar[1 - s], ((k + 1) >> 1) & 1, TMA_WAIT_CYCLES);
+        audit_ticket_on_exit(A, s_audit != 0);
+      }
+      return;
+    }
+    step_tile<R, Off>(A, fin, fout, stages + s * Tile<R>::ELEMS, cur, s_audit != 0, sm, bad, negT);
+    __syncthreads();  // stage s and sm are free again
+  }
+  const unsigned long long step = s_step;
+  watchdog_flags(A.st, step, bad, negT);
+  if (s_audit) audit_finish<N>(A, step, sm, &s_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -358,6 +444,8 @@ struct lbm_ctx {
   double* partial = nullptr;
   double* staging = nullptr;
   int nblocks = 0;      // blocks of one step launch
+  int ntiles = 0, tiles_x = 0;  // node tiles of the grid
+  int sms = 0;          // multiprocessors of the device
   dim3 grid, aux_grid;  // step grid; init / moments / audit grid
   bool wide = false;    // 64-bit element offsets needed
   Coeffs<double> Kd;
@@ -388,7 +476,7 @@ int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
   } while (0)
 
 template <typename R>
-StepArgs<R> make_args(lbm_ctx* c) {
+StepArgs<R> make_args(lbm_ctx* c, int slot) {
   StepArgs<R> A;
   A.K = cast_coeffs<R>(c->Kd);
   A.nx = c->cfg.nx;
@@ -406,33 +494,52 @@ StepArgs<R> make_args(lbm_ctx* c) {
   A.partial = c->partial;
   A.audit_every = c->cfg.audit_every;
   A.nblocks = c->nblocks;
+  A.ntiles = c->ntiles;
+  A.tiles_x = c->tiles_x;
   A.area = c->cfg.dx * c->cfg.dy;
+  A.slot = slot;
   return A;
+}
+
+template <typename R>
+int launch_persistent(lbm_ctx* c, cudaStream_t s, int from, void* fout, const StepArgs<R>& A) {
+  const dim3 blk(Shape<R>::X, Shape<R>::Y);
+  const R* fi = (const R*)c->f[from];
+  const CUtensorMap& tm = c->tmap[from];
+  if (A.nblocks >= A.ntiles) {
+    if (c->wide) k_step<R, long long><<<A.ntiles, blk, 0, s>>>(tm, fi, (R*)fout, A);
+    else k_step<R, unsigned><<<A.ntiles, blk, 0, s>>>(tm, fi, (R*)fout, A);
+  } else {
+    const size_t smem = pipe_smem_bytes<R>();
+    if (c->wide) k_step_pipe<R, long long><<<A.nblocks, blk, smem, s>>>(tm, fi, (R*)fout, A);
+    else k_step_pipe<R, unsigned><<<A.nblocks, blk, smem, s>>>(tm, fi, (R*)fout, A);
+  }
+  CK(c, cudaGetLastError());
+  return LBM_OK;
 }
 
 int launch_step(lbm_ctx* c, cudaStream_t s, int from) {
   const int to = 1 - from;
-  const CUtensorMap& tm = c->tmap[from];
   if (c->tc) {
-    CK(c, tc_launch(tm, (const float*)c->f[from], (float*)c->f[to], make_args<float>(c), c->tc_b,
-                    c->tc_w, c->grid, s));
+    CK(c, tc_launch(c->tmap[from], (const float*)c->f[from], (float*)c->f[to],
+                    make_args<float>(c, from), c->tc_b, c->tc_w, c->grid, s));
     return LBM_OK;
   }
-  if (c->esize == 8) {
-    const dim3 blk(Shape<double>::X, Shape<double>::Y);
-    const double* fi = (const double*)c->f[from];
-    double* fo = (double*)c->f[to];
-    if (c->wide) k_step<double, long long><<<c->grid, blk, 0, s>>>(tm, fi, fo, make_args<double>(c));
-    else k_step<double, unsigned><<<c->grid, blk, 0, s>>>(tm, fi, fo, make_args<double>(c));
-  } else {
-    const dim3 blk(Shape<float>::X, Shape<float>::Y);
-    const float* fi = (const float*)c->f[from];
-    float* fo = (float*)c->f[to];
-    if (c->wide) k_step<float, long long><<<c->grid, blk, 0, s>>>(tm, fi, fo, make_args<float>(c));
-    else k_step<float, unsigned><<<c->grid, blk, 0, s>>>(tm, fi, fo, make_args<float>(c));
-  }
-  CK(c, cudaGetLastError());
-  return LBM_OK;
+  if (c->esize == 8) return launch_persistent<double>(c, s, from, c->f[to], make_args<double>(c, from));
+  return launch_persistent<float>(c, s, from, c->f[to], make_args<float>(c, from));
+}
+
+// Blocks of a step launch when none were chosen: one per tile (k_step).
+int default_blocks(const lbm_ctx* c) { return c->ntiles; }
+
+template <typename R>
+cudaError_t allow_pipe_smem() {
+  const int b = (int)pipe_smem_bytes<R>();
+  cudaError_t e = cudaFuncSetAttribute(k_step_pipe<R, unsigned>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step_pipe<R, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return e;
 }
 
 int ensure_graph(lbm_ctx* c, int from) {
@@ -494,7 +601,9 @@ int encode_tile_map(lbm_ctx* c, int b) {
 int reset_status(lbm_ctx* c, unsigned long long step) {
   DevStatus h;
   memset(&h, 0, offsetof(DevStatus, audit_totals));
-  h.blocks_done = step * (unsigned long long)c->nblocks;
+  h.step[c->cur] = step;
+  h.audit_phase[c->cur] =
+      c->cfg.audit_every > 0 ? (int)(step % (unsigned long long)c->cfg.audit_every) : 0;
   h.first_bad = NONE;
   h.first_negT = NONE;
   CK(c, cudaMemcpyAsync(c->st, &h, offsetof(DevStatus, audit_totals),
@@ -566,11 +675,24 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
   c->plane = c->pitch * C.ny;
   const int bx = c->tc ? TC_X : (c->esize == 8 ? Shape<double>::X : Shape<float>::X);
   const int by = c->tc ? TC_Y : (c->esize == 8 ? Shape<double>::Y : Shape<float>::Y);
-  c->grid = dim3((C.nx + bx - 1) / bx, (C.ny + by - 1) / by);
+  c->tiles_x = (C.nx + bx - 1) / bx;
+  c->ntiles = c->tiles_x * ((C.ny + by - 1) / by);
   c->aux_grid = dim3((C.nx + AUX_X - 1) / AUX_X, (C.ny + AUX_Y - 1) / AUX_Y);
-  c->nblocks = (int)(c->grid.x * c->grid.y);
   c->wide = 16ll * c->plane >= (1ll << 32);
-  const int npartial = std::max(c->nblocks, (int)(c->aux_grid.x * c->aux_grid.y));
+  {
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (c->tc) {  // one CTA per tile
+    c->grid = dim3(c->tiles_x, c->ntiles / c->tiles_x);
+    c->nblocks = c->ntiles;
+  } else {
+    c->nblocks = default_blocks(c);
+    c->grid = dim3(c->nblocks);
+    if (e == cudaSuccess) e = c->esize == 8 ? allow_pipe_smem<double>() : allow_pipe_smem<float>();
+  }
+  const int npartial = std::max(c->ntiles, (int)(c->aux_grid.x * c->aux_grid.y));
   const size_t fbytes = (size_t)16 * c->plane * c->esize;
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&c->f[b], fbytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->geq, 64 * c->esize);
@@ -784,10 +906,10 @@ int lbm_status(lbm_ctx* c, long long* first_bad_step, long long* first_negT_step
 long long lbm_step_count(lbm_ctx* c) {
   if (!c) return -1;
   unsigned long long s = 0;
-  if (cudaMemcpyAsync(&s, &c->st->blocks_done, sizeof(s), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+  if (cudaMemcpyAsync(&s, &c->st->step[c->cur], sizeof(s), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return -1;
-  return (long long)(s / (unsigned long long)c->nblocks);
+  return (long long)s;
 }
 
 int lbm_get_populations(lbm_ctx* c, void* f, long long* step, int on_device) {
@@ -799,9 +921,9 @@ int lbm_get_populations(lbm_ctx* c, void* f, long long* step, int on_device) {
                           c->stream));
   if (step) {
     unsigned long long s = 0;
-    CK(c, cudaMemcpyAsync(&s, &c->st->blocks_done, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&s, &c->st->step[c->cur], sizeof(s), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    *step = (long long)(s / (unsigned long long)c->nblocks);
+    *step = (long long)s;
   } else if (!on_device) {
     CK(c, cudaStreamSynchronize(c->stream));
   }
@@ -820,6 +942,100 @@ int lbm_set_populations(lbm_ctx* c, const void* f, long long step, int on_device
 }
 
 int lbm_element_size(lbm_ctx* c) { return c ? c->esize : 0; }
+
+}  // extern "C"
+
+namespace {
+
+// Sets the number of blocks of the step launch: later steps are issued with
+// `g` blocks and the captured graphs are rebuilt.
+int apply_blocks(lbm_ctx* c, int g) {
+  CK(c, cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 2; ++k)
+    if (c->graph[k]) {
+      cudaGraphExecDestroy(c->graph[k]);
+      c->graph[k] = nullptr;
+    }
+  c->nblocks = g;
+  c->grid = dim3(g);
+  return LBM_OK;
+}
+
+// Times `launches` step launches with `g` blocks that read the current buffer
+// and write the spare one, against a scratch status (no audit), so the
+// state, the step counter and the audit log are untouched. Mean ms / launch.
+template <typename R>
+int time_blocks(lbm_ctx* c, int g, int launches, DevStatus* scratch, cudaEvent_t e0,
+                cudaEvent_t e1, float* ms) {
+  CK(c, cudaMemsetAsync(scratch, 0, offsetof(DevStatus, audit_totals), c->stream));
+  StepArgs<R> A = make_args<R>(c, 0);
+  A.st = scratch;
+  A.audit_every = 0;
+  A.nblocks = g;
+  for (int j = 0; j < 2 + launches; ++j) {
+    if (j == 2) CK(c, cudaEventRecord(e0, c->stream));
+    A.slot = j & 1;
+    const int rc = launch_persistent<R>(c, c->stream, c->cur, c->f[1 - c->cur], A);
+    if (rc != LBM_OK) return rc;
+  }
+  CK(c, cudaEventRecord(e1, c->stream));
+  CK(c, cudaEventSynchronize(e1));
+  CK(c, cudaEventElapsedTime(ms, e0, e1));
+  *ms /= (float)launches;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_set_step_blocks(lbm_ctx* c, int blocks) {
+  if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+  if (blocks < 0) return fail(c, LBM_ERR_INVALID, "blocks < 0");
+  if (c->tc) return fail(c, LBM_ERR_UNSUPPORTED, "the tensor-core step runs one CTA per tile");
+  return apply_blocks(c, blocks == 0 ? default_blocks(c) : std::min(blocks, c->ntiles));
+}
+
+int lbm_step_blocks(lbm_ctx* c) { return c ? c->nblocks : -1; }
+
+int lbm_autotune(lbm_ctx* c, int launches) {
+  if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+  if (launches < 1) return fail(c, LBM_ERR_INVALID, "launches < 1");
+  if (c->tc) return LBM_OK;  // nothing to choose
+  // Candidates: one tile per block (k_step), and for k_step_pipe 1 ..
+  // MINB_PIPE blocks per SM and ceil(ntiles / m) blocks for m = 2 .. 8 tiles
+  // per block.
+  const int per_sm = c->esize == 8 ? Shape<double>::MINB_PIPE : Shape<float>::MINB_PIPE;
+  std::vector<int> cand;
+  auto add = [&](long long g) {
+    const int v = (int)std::max(1ll, std::min((long long)c->ntiles, g));
+    if (std::find(cand.begin(), cand.end(), v) == cand.end()) cand.push_back(v);
+  };
+  for (int m = 1; m <= 8; ++m) add(((long long)c->ntiles + m - 1) / m);
+  for (int m = 1; m <= per_sm; ++m) add((long long)m * c->sms);
+  DevStatus* scratch = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(c, cudaMalloc((void**)&scratch, sizeof(DevStatus)));
+  int rc = LBM_OK, best = cand[0];
+  float best_ms = 0.f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    rc = fail(c, LBM_ERR_CUDA, "cudaEventCreate failed");
+  for (size_t i = 0; i < cand.size() && rc == LBM_OK; ++i) {
+    float ms = 0.f;
+    rc = c->esize == 8 ? time_blocks<double>(c, cand[i], launches, scratch, e0, e1, &ms)
+                       : time_blocks<float>(c, cand[i], launches, scratch, e0, e1, &ms);
+    if (rc == LBM_OK && (i == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = cand[i];
+    }
+  }
+  cudaStreamSynchronize(c->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(scratch);
+  if (rc != LBM_OK) return rc;
+  return apply_blocks(c, best);
+}
 
 const char* lbm_last_error(lbm_ctx* c) {
   return c ? c->err.c_str() : g_create_error.c_str();

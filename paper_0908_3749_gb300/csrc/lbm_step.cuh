@@ -15,18 +15,26 @@ namespace lbmk {
 using namespace d2v16;
 
 constexpr unsigned long long NONE = ~0ull;
-// Thread-block shapes: FP32 32 x 8 (memory-bound, more warps in flight),
-// FP64 32 x 4 (FP64-ALU-bound; smaller blocks balance the SMs better).
+// Node tiles (= thread blocks) of the step and the blocks per SM each launch
+// form is compiled for: MINB for one tile per block (one shared-memory
+// stage), MINB_PIPE for the persistent form (two stages). FP32 32 x 8
+// (memory-bound, more warps in flight); FP64 32 x 2 (FP64-ALU-bound: small
+// tiles spread the work evenly over the SMs).
 template <typename R> struct Shape;
-template <> struct Shape<float> { static constexpr int X = 32, Y = 8, MINB = 4; };
-template <> struct Shape<double> { static constexpr int X = 32, Y = 4, MINB = 4; };
+template <> struct Shape<float> { static constexpr int X = 32, Y = 8, MINB = 4, MINB_PIPE = 3; };
+template <> struct Shape<double> { static constexpr int X = 32, Y = 2, MINB = 8, MINB_PIPE = 6; };
 constexpr int AUX_X = 32, AUX_Y = 8, AUX_N = AUX_X * AUX_Y;  // init / moments / audit
 
 // Device-resident status block of one context.
+// The time level and the audit phase are kept in two slots, one per
+// population buffer: a step reading buffer p reads slot p, and its block 0
+// writes slot 1 - p for the next step. A block learns both with two loads, no
+// division and no atomic; the arrival ticket is used on audit steps only.
 struct DevStatus {
-  unsigned long long blocks_done; // step blocks finished; time level = blocks_done / nblocks
+  unsigned long long step[2];     // time level of buffer 0 / 1 when it is current
+  int audit_phase[2];             // step mod audit_every (0 when audits are off)
+  unsigned int arrive_step;       // blocks of a running audit step finished
   unsigned int arrive_audit;      // blocks finished in a standalone audit
-  unsigned int pad;
   unsigned long long first_bad;   // first level with non-finite / rho <= 0
   unsigned long long first_negT;  // first level with T <= 0
   unsigned long long audit_count; // fused audits written so far
@@ -46,10 +54,12 @@ struct StepArgs {
   R wall[4][3];       // (u, v, T) of LBM_BC_WALL sides
   const R* geq;       // [4][16] Dirichlet ghost populations
   DevStatus* st;
-  double* partial;    // [nblocks][4] audit scratch
+  double* partial;    // [ntiles][4] audit scratch: one partial sum per tile
   int audit_every;
-  int nblocks;
+  int nblocks;        // blocks of the launch
+  int ntiles, tiles_x; // node tiles of the grid (x fastest)
   double area;        // dx * dy
+  int slot;           // index of the buffer read by this step (0 or 1)
 };
 
 // ---------------------------------------------------------------------------
@@ -321,48 +331,75 @@ __device__ __forceinline__ void neighbour_terms(const StepArgs<R>& A, const R* _
 // ---------------------------------------------------------------------------
 // Watchdog and audit epilogue of a step block (N threads)
 // ---------------------------------------------------------------------------
-// Records bad / T <= 0 nodes (one atomic per warp), counts the block as done
-// and, on audit steps, writes the block's FP64 partial sums of (rho, j, e);
-// the last block to finish reduces all partials in a fixed order into the
-// audit ring. `cons` is zero for inactive threads.
-template <int N, typename R>
-__device__ __forceinline__ void step_epilogue(const StepArgs<R>& A, unsigned long long step,
-                                              bool audit, bool bad, bool negT,
-                                              const R (&cons)[4], double (*sm)[4], int* s_last) {
-  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+// Time level of this launch and whether it audits, read by one thread at the
+// start of a step block; block 0 also writes both for the next step into the
+// other slot (no block of this launch reads that slot; the previous launch is
+// done).
+template <typename R>
+__device__ __forceinline__ unsigned long long read_step(const StepArgs<R>& A, int* audit) {
+  const unsigned long long step = *(volatile unsigned long long*)&A.st->step[A.slot];
+  const int ph = *(volatile int*)&A.st->audit_phase[A.slot];
+  *audit = A.audit_every > 0 && ph == 0;
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    A.st->step[1 - A.slot] = step + 1;
+    A.st->audit_phase[1 - A.slot] = ph + 1 >= A.audit_every ? 0 : ph + 1;
+  }
+  return step;
+}
+
+// A block that leaves a step early (a wait timed out) still takes its audit
+// ticket so that later audit steps count their blocks correctly.
+template <typename R>
+__device__ __forceinline__ void audit_ticket_on_exit(const StepArgs<R>& A, bool audit) {
+  if (audit && atomicAdd(&A.st->arrive_step, 1u) == (unsigned)A.nblocks - 1) A.st->arrive_step = 0u;
+}
+
+// Watchdog: records the step as the first with a bad / T <= 0 node (one
+// atomic per warp that saw one).
+__device__ __forceinline__ void watchdog_flags(DevStatus* st, unsigned long long step, bool bad,
+                                               bool negT) {
   const unsigned badm = __ballot_sync(0xffffffffu, bad);
   const unsigned negm = __ballot_sync(0xffffffffu, negT);
-  if ((t & 31) == 0) {
-    if (badm) atomicMin(&A.st->first_bad, step);
-    if (negm) atomicMin(&A.st->first_negT, step);
+  if ((threadIdx.x & 31) == 0) {
+    if (badm) atomicMin(&st->first_bad, step);
+    if (negm) atomicMin(&st->first_negT, step);
   }
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  if (!audit) {
-    if (t == 0) atomicAdd(&A.st->blocks_done, 1ull);
-    return;
-  }
-  const double tot[4] = {(double)cons[0], (double)cons[1], (double)cons[2], (double)cons[3]};
-  const double bs = block_sum4<N>(tot, sm);
-  if (t < 4) A.partial[4 * bid + t] = bs;
+}
+
+// Audit steps, per tile: the block's FP64 sums of (rho, j_x, j_y, e) over the
+// tile go to partial[tile]. Per tile rather than per block, so the totals do
+// not depend on which block handled which tile. `v` is zero for inactive
+// threads. The caller synchronises the block before `sm` is reused.
+template <int N, typename R>
+__device__ __forceinline__ void audit_tile(const StepArgs<R>& A, int tile, const double (&v)[4],
+                                           double (*sm)[4]) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const double bs = block_sum4<N>(v, sm);
+  if (t < 4) A.partial[4 * tile + t] = bs;
+}
+
+// Audit steps, once per block after its last tile: the last block to arrive
+// sums the A.ntiles partials in a fixed order into the audit ring.
+template <int N, typename R>
+__device__ __forceinline__ void audit_finish(const StepArgs<R>& A, unsigned long long step,
+                                             double (*sm)[4], int* s_last) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
   __syncthreads();
   if (t == 0) {
     __threadfence();
-    const unsigned long long prev = atomicAdd(&A.st->blocks_done, 1ull);
-    *s_last = (prev + 1 == (step + 1) * (unsigned long long)A.nblocks);
+    *s_last = atomicAdd(&A.st->arrive_step, 1u) == (unsigned)A.nblocks - 1;
   }
   __syncthreads();
   if (*s_last) {
     __threadfence();
-    const double tot4 = final_sum4<N>(A.partial, A.nblocks, sm);
-    if (t < 4) {
-      const unsigned long long slot = A.st->audit_count % LBM_AUDIT_RING;
-      A.st->audit_totals[slot][t] = tot4 * A.area;
-    }
+    const double tot4 = final_sum4<N>(A.partial, A.ntiles, sm);
+    const unsigned slot = (unsigned)(A.st->audit_count & (LBM_AUDIT_RING - 1));
+    if (t < 4) A.st->audit_totals[slot][t] = tot4 * A.area;
     __syncthreads();
     if (t == 0) {
-      const unsigned long long slot = A.st->audit_count % LBM_AUDIT_RING;
       A.st->audit_steps[slot] = (long long)step;
       A.st->audit_count += 1;
+      A.st->arrive_step = 0u;
     }
   }
 }

@@ -164,10 +164,7 @@ __global__ void __launch_bounds__(TC_N, 1)
     mbar_init(&S.bar_mma, 1);
     mbar_expect_tx(&S.bar_tma, TC_TILE_BYTES);
     tma_load_tile(S.tile, &tmap, x0 - HALO_X, y0 - 1, &S.bar_tma);
-    const unsigned long long done = *(volatile unsigned long long*)&A.st->blocks_done;
-    const unsigned long long step = done / (unsigned long long)A.nblocks;
-    S.step = step;
-    S.audit = A.audit_every > 0 && (step % (unsigned long long)A.audit_every) == 0;
+    S.step = read_step(A, &S.audit);
   }
   // transform constants into shared memory (4 KB)
   for (int i = t; i < 4 * 16 * 64 / 16; i += TC_N)
@@ -253,6 +250,7 @@ __global__ void __launch_bounds__(TC_N, 1)
       mbar_wait_bounded(&S.bar_tma, 0, TMA_WAIT_CYCLES);
       if (issued >= 1) mbar_wait_bounded(&S.bar_mma, 0, TMA_WAIT_CYCLES);
       if (issued >= 2) mbar_wait_bounded(&S.bar_mma, 1, TMA_WAIT_CYCLES);
+      audit_ticket_on_exit(A, audit);
     }
     tc_fence_before();
     __syncthreads();
@@ -287,7 +285,12 @@ __global__ void __launch_bounds__(TC_N, 1)
                  "r"(TC_TMEM_COLS)
                  : "memory");
 
-  step_epilogue<TC_N>(A, step, audit, bad, negT, cons, S.red, &S.last);
+  watchdog_flags(A.st, step, bad, negT);
+  if (audit) {  // one tile per CTA: partial index = block index
+    const double v[4] = {(double)cons[0], (double)cons[1], (double)cons[2], (double)cons[3]};
+    audit_tile<TC_N>(A, blockIdx.y * gridDim.x + blockIdx.x, v, S.red);
+    audit_finish<TC_N>(A, step, S.red, &S.last);
+  }
 }
 
 }  // namespace

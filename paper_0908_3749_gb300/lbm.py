@@ -66,6 +66,9 @@ _SIGS = {
     "lbm_set_populations": (ctypes.c_int, [_vp, _vp, _ll, ctypes.c_int]),
     "lbm_element_size": (ctypes.c_int, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_set_step_blocks": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "lbm_step_blocks": (ctypes.c_int, [_vp]),
+    "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int]),
 }
 
 
@@ -224,6 +227,20 @@ def lbm_element_size(ctx):
 
 def lbm_last_error(ctx=None):
     return _err(ctx)
+
+
+def lbm_set_step_blocks(ctx, blocks):
+    _check(load().lbm_set_step_blocks(ctx, int(blocks)), ctx)
+
+
+def lbm_step_blocks(ctx):
+    return int(load().lbm_step_blocks(ctx))
+
+
+def lbm_autotune(ctx, launches=20):
+    """Chooses the step's block count by timing; returns it."""
+    _check(load().lbm_autotune(ctx, int(launches)), ctx)
+    return lbm_step_blocks(ctx)
 
 
 # ----------------------------------------------------------------------------

@@ -1,0 +1,75 @@
+"""Command-line runner: one of the synthetic workloads stepped through the C ABI.
+
+    python -m paper_0908_3749_gb300.run --workload reflection --precision fp32 --steps 100
+
+Prints one JSON line with the step count, the watchdog status, the
+conservation totals and the ranges of rho, u, v, T. Nothing is timed; it is
+the plain driver for quick checks and for profiler runs of a single kernel
+(every launch of the step is one time step, in order). Run from the
+repository root (the workload generators live in ``workloads.py`` there).
+"""
+import argparse
+import json
+
+import numpy as np
+
+from . import lbm
+
+WORKLOADS = ("reflection", "bubble", "sod", "couette", "random")
+
+
+def make_workload(name, nx=None, ny=None):
+    import workloads as W
+    if name == "reflection":
+        return W.regular_reflection(nx=nx or 600, ny=ny or 200)
+    if name == "bubble":
+        return W.shock_bubble(nx=nx or 2048, ny=ny or 1024)
+    if name == "sod":
+        return W.sod_config1()
+    if name == "couette":
+        return W.couette()
+    return W.random_state(nx or 256, ny or 128, seed=0)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--workload", choices=WORKLOADS, default="reflection")
+    ap.add_argument("--nx", type=int, default=None)
+    ap.add_argument("--ny", type=int, default=None)
+    ap.add_argument("--precision", choices=("fp64", "fp32", "tc_tf32x3"), default="fp32")
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--audit-every", type=int, default=0)
+    ap.add_argument("--blocks", type=int, default=0,
+                    help="step launch blocks (0: one per tile); see lbm_set_step_blocks")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="if > 0, choose the launch shape with lbm_autotune(launches)")
+    args = ap.parse_args(argv)
+
+    w = make_workload(args.workload, args.nx, args.ny)
+    cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, args.precision,
+                          args.audit_every)
+    ctx = lbm.lbm_create(cfg)
+    try:
+        lbm.lbm_set_init(ctx, *[np.ascontiguousarray(a) for a in w.fields()])
+        if args.blocks and args.precision != "tc_tf32x3":
+            lbm.lbm_set_step_blocks(ctx, args.blocks)
+        if args.autotune > 0:
+            lbm.lbm_autotune(ctx, args.autotune)
+        lbm.lbm_step(ctx, args.steps)
+        rc, bad, neg = lbm.lbm_status(ctx)
+        m = [np.empty((w.ny, w.nx)) for _ in range(4)]
+        lbm.lbm_moments(ctx, *m)
+        out = {"workload": args.workload, "nx": w.nx, "ny": w.ny, "precision": args.precision,
+               "steps": lbm.lbm_step_count(ctx), "step_blocks": lbm.lbm_step_blocks(ctx),
+               "status": rc, "first_bad_step": bad, "first_negT_step": neg,
+               "totals": lbm.lbm_audit(ctx),
+               "ranges": {k: [float(np.nanmin(a)), float(np.nanmax(a))]
+                          for k, a in zip(("rho", "u", "v", "T"), m)}}
+    finally:
+        lbm.lbm_destroy(ctx)
+    print(json.dumps(out))
+    return 0 if rc == lbm.LBM_OK else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

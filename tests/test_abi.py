@@ -55,3 +55,11 @@ def test_create_rejects_bad_configs_on_host(change, code):
         lbm.lbm_create(cfg)
     assert ei.value.code == code
     assert lbm.lbm_last_error(None)
+
+
+def test_launch_shape_entry_points_reject_null_context():
+    from paper_0908_3749_gb300 import lbm
+    lib = lbm.load()
+    assert lib.lbm_set_step_blocks(None, 4) == lbm.LBM_ERR_INVALID
+    assert lib.lbm_step_blocks(None) == -1
+    assert lib.lbm_autotune(None, 5) == lbm.LBM_ERR_INVALID

@@ -62,6 +62,68 @@ def test_checkpoint_resume_is_bitwise(precision):
         lbm.lbm_destroy(ctx)
 
 
+def _state(lbm, ctx, shape, dt):
+    f = np.empty(shape, dtype=dt)
+    step = lbm.lbm_get_populations(ctx, f)
+    log, steps = lbm.lbm_audit_log(ctx)
+    return f, step, log, steps, lbm.lbm_status(ctx)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_block_count_changes_no_result(precision):
+    """Tiles reach the persistent step's blocks through a counter; every block
+    count (one block doing all tiles, a few, the default) gives bitwise the
+    same populations, audit log and watchdog state."""
+    w = W.regular_reflection(nx=300, ny=100)
+    dt = np.float64 if precision == "fp64" else np.float32
+    states = []
+    for blocks in (1, 7, 64, 0):
+        lbm, ctx = _ctx(w, precision, audit_every=7)
+        try:
+            lbm.lbm_set_step_blocks(ctx, blocks)
+            assert lbm.lbm_step_blocks(ctx) >= 1
+            lbm.lbm_step(ctx, 150)      # two graph replays and 22 single launches
+            states.append(_state(lbm, ctx, (16, w.ny, w.nx), dt))
+        finally:
+            lbm.lbm_destroy(ctx)
+    f0, step0, log0, steps0, st0 = states[0]
+    assert step0 == 150 and steps0 == list(range(0, 150, 7)) and st0[0] == 0
+    for f, step, log, steps, st in states[1:]:
+        assert np.array_equal(f, f0)
+        assert (step, log, steps, st) == (step0, log0, steps0, st0)
+
+
+def test_autotune_leaves_state_and_counters_alone():
+    from paper_0908_3749_gb300 import lbm as L
+    w = W.regular_reflection(nx=200, ny=64)
+    shape = (16, w.ny, w.nx)
+    lbm, ctx = _ctx(w, "fp32", audit_every=5)
+    lbm, ref = _ctx(w, "fp32", audit_every=5)
+    try:
+        lbm.lbm_step(ctx, 12)
+        lbm.lbm_step(ref, 12)
+        before = _state(lbm, ctx, shape, np.float32)
+        g = lbm.lbm_autotune(ctx, 5)
+        assert 1 <= g == lbm.lbm_step_blocks(ctx)
+        after = _state(lbm, ctx, shape, np.float32)
+        assert np.array_equal(before[0], after[0]) and before[1:] == after[1:]
+        lbm.lbm_step(ctx, 70)
+        lbm.lbm_step(ref, 70)
+        a, b = _state(lbm, ctx, shape, np.float32), _state(lbm, ref, shape, np.float32)
+        assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
+    finally:
+        lbm.lbm_destroy(ctx)
+        lbm.lbm_destroy(ref)
+    tc, tctx = _ctx(w, "tc_tf32x3")
+    try:
+        assert tc.lbm_autotune(tctx, 3) == tc.lbm_step_blocks(tctx)
+        with pytest.raises(L.LBMError) as ei:
+            tc.lbm_set_step_blocks(tctx, 4)
+        assert ei.value.code == L.LBM_ERR_UNSUPPORTED
+    finally:
+        tc.lbm_destroy(tctx)
+
+
 def test_device_pointers_and_streams():
     import torch
     w = W.random_state(50, 20, seed=4)
