@@ -100,7 +100,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<R>& A, const R* __restr
     for (int i = 0; i < 16; ++i) fout[i * P + c] = acc[i];
   }
   if (audit) {  // FP64 only on audit steps
-    const double tot[4] = {(double)mc[0], (double)mc[1], (double)mc[2], (double)mc[3]};
+    const double tot[4] = {widen(mc[0]), widen(mc[1]), widen(mc[2]), widen(mc[3])};
     audit_tile<N>(A, cur, tot, sm);
   }
 }

@@ -62,6 +62,17 @@ struct StepArgs {
   int slot;           // index of the buffer read by this step (0 or 1)
 };
 
+// FP32 -> FP64 conversion that stays inside the branch that needs it. A plain
+// conversion may be hoisted above an audit-step test by the compiler, and
+// conversions to FP64 run on the FP64 pipe, which is slow on GB300: hoisted,
+// they cost every step (measured: 4 per node, 15-30 % of that pipe's time).
+__device__ __forceinline__ double widen(float x) {
+  double d;
+  asm volatile("cvt.f64.f32 %0, %1;" : "=d"(d) : "f"(x));
+  return d;
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 // ---------------------------------------------------------------------------
 // Fixed-order FP64 reductions of four sums (bitwise reproducible)
 // ---------------------------------------------------------------------------

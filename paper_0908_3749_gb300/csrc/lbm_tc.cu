@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(TC_N, 1)
 
   watchdog_flags(A.st, step, bad, negT);
   if (audit) {  // one tile per CTA: partial index = block index
-    const double v[4] = {(double)cons[0], (double)cons[1], (double)cons[2], (double)cons[3]};
+    const double v[4] = {widen(cons[0]), widen(cons[1]), widen(cons[2]), widen(cons[3])};
     audit_tile<TC_N>(A, blockIdx.y * gridDim.x + blockIdx.x, v, S.red);
     audit_finish<TC_N>(A, step, S.red, &S.last);
   }
