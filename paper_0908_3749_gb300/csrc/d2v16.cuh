@@ -158,6 +158,42 @@ __device__ __forceinline__ float recip(float x) {
   return r;
 }
 
+// Two FP32 values carried together (two nodes): every operation is one paired
+// instruction of the FP32 units (add / mul / fma on .f32x2), so two nodes cost
+// the instructions of one. A product is kept unevaluated (P2) until it meets a
+// sum, which then becomes one paired fused multiply-add, as the compiler does
+// for scalar float; scalar coefficients are broadcast to both lanes.
+struct F2 {
+  float2 v;
+  __device__ __forceinline__ F2() {}
+  __device__ __forceinline__ explicit F2(float2 x) : v(x) {}
+  __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ F2(double s) : v(make_float2((float)s, (float)s)) {}
+};
+struct P2 {
+  float2 a, b;
+  __device__ __forceinline__ operator F2() const { return F2(__fmul2_rn(a, b)); }
+};
+__device__ __forceinline__ float2 bcast(float k) { return make_float2(k, k); }
+__device__ __forceinline__ F2 operator-(F2 x) { return F2(-x.v.x, -x.v.y); }
+__device__ __forceinline__ F2 operator+(F2 x, F2 y) { return F2(__fadd2_rn(x.v, y.v)); }
+__device__ __forceinline__ F2 operator-(F2 x, F2 y) { return F2(__fadd2_rn(x.v, (-y).v)); }
+__device__ __forceinline__ P2 operator*(F2 x, F2 y) { return {x.v, y.v}; }
+__device__ __forceinline__ P2 operator*(float k, F2 y) { return {bcast(k), y.v}; }
+__device__ __forceinline__ P2 operator*(F2 y, float k) { return {y.v, bcast(k)}; }
+__device__ __forceinline__ P2 operator*(P2 p, F2 y) { return {F2(p).v, y.v}; }
+__device__ __forceinline__ P2 operator*(F2 y, P2 p) { return {y.v, F2(p).v}; }
+__device__ __forceinline__ P2 operator*(P2 p, P2 q) { return {F2(p).v, F2(q).v}; }
+__device__ __forceinline__ F2 operator+(P2 p, F2 c) { return F2(__ffma2_rn(p.a, p.b, c.v)); }
+__device__ __forceinline__ F2 operator+(F2 c, P2 p) { return F2(__ffma2_rn(p.a, p.b, c.v)); }
+__device__ __forceinline__ F2 operator+(P2 p, P2 q) { return F2(__ffma2_rn(p.a, p.b, F2(q).v)); }
+__device__ __forceinline__ F2 operator-(P2 p, F2 c) { return F2(__ffma2_rn(p.a, p.b, (-c).v)); }
+__device__ __forceinline__ F2 operator-(F2 c, P2 p) {
+  return F2(__ffma2_rn((-F2(p.a)).v, p.b, c.v));
+}
+__device__ __forceinline__ F2 operator-(P2 p, P2 q) { return F2(__ffma2_rn(p.a, p.b, (-F2(q)).v)); }
+__device__ __forceinline__ F2 recip(F2 x) { return F2(recip(x.v.x), recip(x.v.y)); }
+
 template <typename R>
 struct Groups {
   R S[4], C[4], X[4], Y[4];
@@ -233,9 +269,10 @@ __device__ __forceinline__ Eq<R> equilibria(R rho, R jx, R jy, R e) {
   return q;
 }
 
-// f^eq = M^-1 f_hat^eq for the conserved moments (rho, j, e).
-template <typename R>
-__device__ __forceinline__ void feq(const Coeffs<R>& K, R rho, R jx, R jy, R e,
+// f^eq = M^-1 f_hat^eq for the conserved moments (rho, j, e). KT: the
+// coefficient type (R itself, or float for R = F2).
+template <typename KT, typename R>
+__device__ __forceinline__ void feq(const Coeffs<KT>& K, R rho, R jx, R jy, R e,
                                     R out[16]) {
   const Eq<R> q = equilibria(rho, jx, jy, e);
   R S[4], C[4], X[4], Y[4];
@@ -258,14 +295,14 @@ struct Cons {
   R rho, jx, jy, e;
 };
 
-// Row r of a forward block (given in the arithmetic type) times a group vector.
-template <typename R>
-__device__ __forceinline__ R row4(const R (&b)[4][4], int r, const R (&v)[4]) {
+// Row r of a forward block (coefficients of type KT) times a group vector.
+template <typename KT, typename R>
+__device__ __forceinline__ R row4(const KT (&b)[4][4], int r, const R (&v)[4]) {
   return b[r][0] * v[0] + b[r][1] * v[1] + b[r][2] * v[2] + b[r][3] * v[3];
 }
 
-template <typename R>
-__device__ __forceinline__ Cons<R> conserved(const Coeffs<R>& K, const Groups<R>& d) {
+template <typename KT, typename R>
+__device__ __forceinline__ Cons<R> conserved(const Coeffs<KT>& K, const Groups<R>& d) {
   Cons<R> c;
   c.rho = (d.S[0] + d.S[1]) + (d.S[2] + d.S[3]);
   c.e = row4(K.F0, 1, d.S);
@@ -276,8 +313,8 @@ __device__ __forceinline__ Cons<R> conserved(const Coeffs<R>& K, const Groups<R>
 
 // Collision of Eq. 3 at one node: df = M^-1 (-dt S_hat (m - m^eq)), given the
 // group values and the conserved moments of the node. Returns P = rho T too.
-template <typename R>
-__device__ __forceinline__ R collide(const Coeffs<R>& K, const Groups<R>& d,
+template <typename KT, typename R>
+__device__ __forceinline__ R collide(const Coeffs<KT>& K, const Groups<R>& d,
                                      const Cons<R>& c, R df[16]) {
   const Eq<R> q = equilibria(c.rho, c.jx, c.jy, c.e);
   const R d11 = row4(K.F0, 2, d.S) - q.m11;

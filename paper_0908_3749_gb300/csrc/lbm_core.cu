@@ -105,11 +105,113 @@ __device__ __forceinline__ void step_tile(const StepArgs<R>& A, const R* __restr
   }
 }
 
+// FP32 tiles: thread (tx, ty) updates nodes (x, y) and (x, y + Y/2) together
+// in paired arithmetic (F2). Interior pairs take their Lax-Wendroff terms from
+// shared memory in paired form; a pair with a node on the domain edge
+// finishes node by node through the scalar neighbour_terms (ghosts, periodic
+// wraps). Audit steps: per-tile sums of the Y rows in a fixed order (two warp
+// passes, then rows 0 .. Y-1).
+template <typename Off>
+__device__ __forceinline__ void step_tile_x2(const StepArgs<float>& A, const float* __restrict__ fin,
+                                             float* __restrict__ fout, const float* stage, int cur,
+                                             bool audit, double (*sm)[4], bool& bad, bool& negT) {
+  constexpr int BXD = Shape<float>::X, BYD = Shape<float>::Y, HY = BYD / 2;
+  constexpr int BXP = Tile<float>::BXP, PS = Tile<float>::ROWS * BXP;
+  static_assert(Shape<float>::TY == HY, "two rows per thread");
+  const int x = (cur % A.tiles_x) * BXD + threadIdx.x;
+  const int ya = (cur / A.tiles_x) * BYD + threadIdx.y, yb = ya + HY;
+  const bool act_a = x < A.nx && ya < A.ny, act_b = x < A.nx && yb < A.ny;  // act_b => act_a
+  float mca[4] = {0.f, 0.f, 0.f, 0.f}, mcb[4] = {0.f, 0.f, 0.f, 0.f};
+  if (act_a) {
+    const Off P = (Off)A.plane, pitch = (Off)A.pitch;
+    const Off ca = (Off)ya * pitch + (Off)x, cb = ca + (Off)HY * pitch;
+    const float* sa = stage + (threadIdx.y + 1) * BXP + threadIdx.x + HALO_X;
+    const float* sb = sa + HY * BXP;
+    F2 f[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) f[i] = F2(sa[i * PS], sb[i * PS]);
+    Groups<F2> d;
+    transform(f, d);
+    const Cons<F2> m = conserved(A.K, d);
+    F2 acc[16];
+    const F2 press = collide(A.K, d, m, acc);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = A.K.a0[i] * f[i] + acc[i];
+
+    const bool ba = !(m.rho.v.x > 0.f) || !isfinite(m.rho.v.x + m.jx.v.x + m.jy.v.x + m.e.v.x);
+    const bool bb = act_b && (!(m.rho.v.y > 0.f) || !isfinite(m.rho.v.y + m.jx.v.y + m.jy.v.y + m.e.v.y));
+    bad |= ba || bb;
+    negT |= (!ba && !(press.v.x > 0.f)) || (act_b && !bb && !(press.v.y > 0.f));
+    mca[0] = m.rho.v.x; mca[1] = m.jx.v.x; mca[2] = m.jy.v.x; mca[3] = m.e.v.x;
+    if (act_b) { mcb[0] = m.rho.v.y; mcb[1] = m.jx.v.y; mcb[2] = m.jy.v.y; mcb[3] = m.e.v.y; }
+
+    if (act_b && x > 0 && x < A.nx - 1 && ya > 0 && yb < A.ny - 1) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        F2 a = acc[i];
+        if (has_x(i)) {
+          a = A.K.aW[i] * F2(sa[i * PS - 1], sb[i * PS - 1]) + a;
+          a = A.K.aE[i] * F2(sa[i * PS + 1], sb[i * PS + 1]) + a;
+        }
+        if (has_y(i)) {
+          a = A.K.aS[i] * F2(sa[i * PS - BXP], sb[i * PS - BXP]) + a;
+          a = A.K.aN[i] * F2(sa[i * PS + BXP], sb[i * PS + BXP]) + a;
+        }
+        fout[i * P + ca] = a.v.x;
+        fout[i * P + cb] = a.v.y;
+      }
+    } else {
+      float acc1[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc1[i] = acc[i].v.x;
+      const Cons<float> m1 = {m.rho.v.x, m.jx.v.x, m.jy.v.x, m.e.v.x};
+      neighbour_terms<float, Off, BXP>(A, fin, sa, PS, P, pitch, ca, x, ya, m1, acc1);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) fout[i * P + ca] = acc1[i];
+      if (act_b) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc1[i] = acc[i].v.y;
+        const Cons<float> m2 = {m.rho.v.y, m.jx.v.y, m.jy.v.y, m.e.v.y};
+        neighbour_terms<float, Off, BXP>(A, fin, sb, PS, P, pitch, cb, x, yb, m2, acc1);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) fout[i * P + cb] = acc1[i];
+      }
+    }
+  }
+  if (audit) {  // FP64 only on audit steps
+    const int lane = threadIdx.x;
+    const double va[4] = {widen(mca[0]), widen(mca[1]), widen(mca[2]), widen(mca[3])};
+    const double vb[4] = {widen(mcb[0]), widen(mcb[1]), widen(mcb[2]), widen(mcb[3])};
+    const double ka = warp_sum4(va, lane), kb = warp_sum4(vb, lane);
+    if ((lane & 7) == 0) {
+      sm[threadIdx.y][lane >> 3] = ka;
+      sm[threadIdx.y + HY][lane >> 3] = kb;
+    }
+    __syncthreads();
+    const int t = threadIdx.y * BXD + threadIdx.x;
+    if (t < 4) {
+      double s = 0.0;
+      for (int w = 0; w < BYD; ++w) s += sm[w][t];
+      A.partial[4 * cur + t] = s;
+    }
+  }
+}
+
 template <typename R, typename Off>
-__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
+__device__ __forceinline__ void step_any(const StepArgs<R>& A, const R* __restrict__ fin,
+                                         R* __restrict__ fout, const R* stage, int cur, bool audit,
+                                         double (*sm)[4], bool& bad, bool& negT) {
+  if constexpr (Shape<R>::TY == Shape<R>::Y)
+    step_tile<R, Off>(A, fin, fout, stage, cur, audit, sm, bad, negT);
+  else
+    step_tile_x2<Off>(A, fin, fout, stage, cur, audit, sm, bad, negT);
+}
+
+template <typename R, typename Off>
+__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB)
     k_step(const __grid_constant__ CUtensorMap tmap, const R* __restrict__ fin,
            R* __restrict__ fout, const StepArgs<R> A) {
-  constexpr int N = Shape<R>::X * Shape<R>::Y;
+  constexpr int N = Shape<R>::X * Shape<R>::TY;
   __shared__ __align__(128) R tile[Tile<R>::ELEMS];
   __shared__ double sm[N / 4][4];
   __shared__ unsigned long long bar;
@@ -137,7 +239,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB)
     return;
   }
   bool bad = false, negT = false;
-  step_tile<R, Off>(A, fin, fout, tile, blockIdx.x, audit, sm, bad, negT);
+  step_any<R, Off>(A, fin, fout, tile, blockIdx.x, audit, sm, bad, negT);
   const unsigned long long step = s_step;
   watchdog_flags(A.st, step, bad, negT);
   if (audit) audit_finish<N>(A, step, sm, &s_last);
@@ -151,10 +253,10 @@ static_assert(sizeof(float) * Tile<float>::ELEMS % 128 == 0, "stage size");
 static_assert(sizeof(double) * Tile<double>::ELEMS % 128 == 0, "stage size");
 
 template <typename R, typename Off>
-__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB_PIPE)
+__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB_PIPE)
     k_step_pipe(const __grid_constant__ CUtensorMap tmap, const R* __restrict__ fin,
                 R* __restrict__ fout, const StepArgs<R> A) {
-  constexpr int N = Shape<R>::X * Shape<R>::Y;
+  constexpr int N = Shape<R>::X * Shape<R>::TY;
   extern __shared__ __align__(128) unsigned char pipe_smem[];
   R* const stages = reinterpret_cast<R*>(  // [2][Tile<R>::ELEMS], 128-byte aligned
       pipe_smem + ((128u - (smem_addr(pipe_smem) & 127u)) & 127u));
@@ -191,7 +293,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::Y, Shape<R>::MINB_PIPE
       }
       return;
     }
-    step_tile<R, Off>(A, fin, fout, stages + s * Tile<R>::ELEMS, cur, s_audit != 0, sm, bad, negT);
+    step_any<R, Off>(A, fin, fout, stages + s * Tile<R>::ELEMS, cur, s_audit != 0, sm, bad, negT);
     __syncthreads();  // stage s and sm are free again
   }
   const unsigned long long step = s_step;
@@ -503,7 +605,7 @@ StepArgs<R> make_args(lbm_ctx* c, int slot) {
 
 template <typename R>
 int launch_persistent(lbm_ctx* c, cudaStream_t s, int from, void* fout, const StepArgs<R>& A) {
-  const dim3 blk(Shape<R>::X, Shape<R>::Y);
+  const dim3 blk(Shape<R>::X, Shape<R>::TY);
   const R* fi = (const R*)c->f[from];
   const CUtensorMap& tm = c->tmap[from];
   if (A.nblocks >= A.ntiles) {

@@ -15,14 +15,20 @@ namespace lbmk {
 using namespace d2v16;
 
 constexpr unsigned long long NONE = ~0ull;
-// Node tiles (= thread blocks) of the step and the blocks per SM each launch
-// form is compiled for: MINB for one tile per block (one shared-memory
-// stage), MINB_PIPE for the persistent form (two stages). FP32 32 x 8
-// (memory-bound, more warps in flight); FP64 32 x 2 (FP64-ALU-bound: small
-// tiles spread the work evenly over the SMs).
+// Node tiles of X x Y nodes handled by blocks of X x TY threads, and the
+// blocks per SM each launch form is compiled for: MINB for one tile per block
+// (one shared-memory stage), MINB_PIPE for the persistent form (two stages).
+// FP32: 32 x 8 tiles, each thread two nodes (rows y and y + 4) in paired
+// FP32 arithmetic (memory-bound: fewer instructions per node). FP64: 32 x 2
+// tiles, one node per thread (FP64-ALU-bound: small tiles spread the work
+// evenly over the SMs).
 template <typename R> struct Shape;
-template <> struct Shape<float> { static constexpr int X = 32, Y = 8, MINB = 4, MINB_PIPE = 3; };
-template <> struct Shape<double> { static constexpr int X = 32, Y = 2, MINB = 8, MINB_PIPE = 6; };
+template <> struct Shape<float> {
+  static constexpr int X = 32, Y = 8, TY = 4, MINB = 4, MINB_PIPE = 3;
+};
+template <> struct Shape<double> {
+  static constexpr int X = 32, Y = 2, TY = 2, MINB = 8, MINB_PIPE = 6;
+};
 constexpr int AUX_X = 32, AUX_Y = 8, AUX_N = AUX_X * AUX_Y;  // init / moments / audit
 
 // Device-resident status block of one context.
