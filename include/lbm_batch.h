@@ -71,8 +71,10 @@ int lbm_batch_audit(lbm_batch* b, double* totals);
  * error of the batch). */
 int lbm_batch_status(lbm_batch* b, long long* first_bad, int* nbad, int* timeout);
 
-/* Tiling: tile = nodes per work item (64, 128, 256, 512 or 1024), threads =
- * threads per block (64, 128 or 256, <= tile). */
+/* Tiling: tile = nodes per work item, threads = threads per block; each
+ * thread updates node pairs, so tile is 2 or 4 x threads. The pairs built:
+ * (128, 64), (256, 64), (256, 128), (512, 128), (512, 256), (1024, 256),
+ * (1024, 512), (1024, 128); anything else is LBM_ERR_INVALID. */
 int lbm_batch_set_tiling(lbm_batch* b, int tile, int threads);
 int lbm_batch_get_tiling(lbm_batch* b, int* tile, int* threads, int* blocks);
 

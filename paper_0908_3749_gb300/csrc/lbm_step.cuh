@@ -9,10 +9,12 @@
 
 #include "../../include/lbm.h"
 #include "d2v16.cuh"
+#include "tma.cuh"
 
 namespace lbmk {
 
 using namespace d2v16;
+using namespace gbtma;
 
 constexpr unsigned long long NONE = ~0ull;
 // Node tiles of X x Y nodes handled by blocks of X x TY threads, and the
@@ -204,50 +206,6 @@ struct Tile {
   static constexpr int ELEMS = 16 * ROWS * BXP;
   static constexpr unsigned BYTES = ELEMS * sizeof(R);
 };
-constexpr long long TMA_WAIT_CYCLES = 2000000000ll;  // ~1 s at 2 GHz
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for phase `parity` of the barrier for at most `limit` SM cycles.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
-                                                  long long limit) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > limit) return false;
-    __nanosleep(64);
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map, int x, int y,
-                                              unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(0), "r"(smem_addr(bar))
-      : "memory");
-}
-
 // ---------------------------------------------------------------------------
 // Lax-Wendroff neighbour terms (Eq. A.1b) with boundary ghosts
 // ---------------------------------------------------------------------------

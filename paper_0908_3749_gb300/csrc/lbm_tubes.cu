@@ -3,8 +3,10 @@
 //
 // Layout: FP32 populations SoA f[i][p], p running over all tubes; tube t owns
 // nodes off[t] .. off[t] + nx[t] - 1 with off[t] a multiple of 32 (128-byte
-// aligned rows). Work items are tiles of `tile` consecutive nodes of one tube;
-// the item list is ordered tube by tube.
+// aligned rows), and 32 unused nodes lie before the first tube and after the
+// last, so that the staged copies below never leave the allocation. Work items
+// are tiles of `tile` consecutive nodes of one tube; the item list is ordered
+// tube by tube.
 //
 // Per node the arithmetic is the 2D step with every y-derivative zero (one
 // node deep, y periodic): the collision of Eq. 3 through the factorised
@@ -14,9 +16,13 @@
 // the scaled block inverses of M are lattice constants shared by all tubes.
 //
 // The persistent kernel runs all requested steps: each resident block takes
-// items blockIdx, blockIdx + gridDim, ...; after each step all blocks meet at
-// a grid barrier whose spin is bounded in time. Co-residency is guaranteed by
-// a cooperative launch sized from the occupancy calculator.
+// items blockIdx, blockIdx + gridDim, ...; the 16 population rows of an item
+// and 4 halo nodes on each side come into shared memory by bulk TMA copies
+// (two stages: the next item's copy runs while the current one is computed);
+// each thread updates node pairs (x, x + threads) in paired FP32 arithmetic.
+// After each step all blocks meet at a grid barrier whose spin is bounded in
+// time. Co-residency is guaranteed by a cooperative launch sized from the
+// occupancy calculator.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,12 +35,15 @@
 
 #include "../../include/lbm_batch.h"
 #include "d2v16.cuh"
+#include "tma.cuh"
 
 using namespace d2v16;
+using namespace gbtma;
 
 namespace {
 
 constexpr unsigned long long NONE = ~0ull;
+constexpr long long TUBE_PAD = 32;  // unused nodes before the first and after the last tube
 
 struct TubeDesc {
   long long off;   // first population index of the tube
@@ -113,10 +122,34 @@ __device__ bool grid_barrier(const BatchArgs& A, unsigned& gen, bool skip) {
   return ok != 0;
 }
 
+// Staged width of an item: its TILE nodes plus 4 halo nodes on each side.
+template <int TILE>
+__host__ __device__ constexpr int stage_width() { return TILE + 8; }
+
+// Thread 0: copies item `item` (16 population rows of its valid nodes plus
+// 4 halo nodes on each side, rounded up to 16 bytes) into `stage`. The
+// source start off + x0 - 4 is a multiple of 4 floats (off and x0 are
+// multiples of 32 and of TILE), so both ends are 16-byte aligned.
+template <int TILE>
+__device__ __forceinline__ void issue_item(const BatchArgs& A, const float* fin, float* stage,
+                                           int item, unsigned long long* bar) {
+  const int2 it = A.items[item];
+  const TubeDesc& D = A.tubes[it.x];
+  const int valid = min(TILE, D.nx - it.y);
+  const unsigned n = (unsigned)((valid + 8 + 3) & ~3);  // floats per row, <= TILE + 8
+  mbar_expect_tx(bar, 16u * 4u * n);
+  const float* src = fin + D.off + it.y - 4;
+#pragma unroll 1
+  for (int i = 0; i < 16; ++i)
+    bulk_load(stage + i * stage_width<TILE>(), src + i * A.plane, 4u * n, bar);
+}
+
+// Updates one item from its staged copy: thread t takes node pairs
+// (x, x + BT) of each 2 BT-node chunk in paired arithmetic.
 template <int BT, int TILE>
-__device__ __forceinline__ void tube_tile(const BatchArgs& A, const float* __restrict__ fin,
-                                          float* __restrict__ fout, int item,
-                                          unsigned long long level) {
+__device__ __forceinline__ void tube_item(const BatchArgs& A, float* __restrict__ fout,
+                                          const float* stage, int item, unsigned long long level) {
+  constexpr int W = stage_width<TILE>();
   const int2 it = A.items[item];
   const TubeDesc& D = A.tubes[it.x];
   const long long off = D.off;
@@ -136,63 +169,67 @@ __device__ __forceinline__ void tube_tile(const BatchArgs& A, const float* __res
   const float* gL = A.ghost + (size_t)it.x * 32;
   const float* gR = gL + 16;
   const long long P = A.plane;
+  const Coeffs<float>& E = A.E;
   bool bad = false;
 #pragma unroll 1
-  for (int j = 0; j < TILE / BT; ++j) {
-    const int x = it.y + j * BT + threadIdx.x;
-    if (x < nx) {
-      const long long c = off + x;
-      float f[16];
+  for (int c0 = 0; c0 < TILE; c0 += 2 * BT) {
+    const int la = c0 + threadIdx.x, lb = la + BT;  // node index within the item
+    const int xa = it.y + la, xb = it.y + lb;
+    if (xa >= nx) continue;
+    const bool actb = xb < nx;
+    const float* sa = stage + la + 4;
+    const float* sb = stage + lb + 4;
+    F2 f[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) f[i] = fin[i * P + c];
-      Groups<float> d;
-      transform(f, d);
-      const Cons<float> m = conserved(A.E, d);
-      const Eq<float> q = equilibria(m.rho, m.jx, m.jy, m.e);
-      // deviations from equilibrium of the non-conserved moments, relaxed
-      const Coeffs<float>& E = A.E;
-      const float r11 = w[6] * (row4(E.F0, 2, d.S) - q.m11);
-      const float r12 = w[7] * row4(E.F0, 3, d.S);
-      const float r7 = w[2] * (row4(E.FX, 1, d.X) - q.m7);
-      const float r9 = w[4] * (row4(E.FX, 2, d.X) - q.m9);
-      const float r15 = w[10] * row4(E.FX, 3, d.X);
-      const float r8 = w[3] * (row4(E.FY, 1, d.Y) - q.m8);
-      const float r10 = w[5] * (row4(E.FY, 2, d.Y) - q.m10);
-      const float r16 = w[11] * row4(E.FY, 3, d.Y);
-      const float r5 = w[0] * (E.FC[0][0] * d.C[0] + E.FC[0][1] * d.C[1] - q.m5);
-      const float r13 = w[8] * (E.FC[1][0] * d.C[0] + E.FC[1][1] * d.C[1] - q.m13);
-      const float r6 = w[1] * (E.FS[0][0] * d.C[2] + E.FS[0][1] * d.C[3] - q.m6);
-      const float r14 = w[9] * (E.FS[1][0] * d.C[2] + E.FS[1][1] * d.C[3] - q.m14);
-      float S[4], C[4], X[4], Y[4], df[16];
+    for (int i = 0; i < 16; ++i) f[i] = F2(sa[i * W], sb[i * W]);
+    Groups<F2> d;
+    transform(f, d);
+    const Cons<F2> m = conserved(E, d);
+    const Eq<F2> q = equilibria(m.rho, m.jx, m.jy, m.e);
+    // deviations from equilibrium of the non-conserved moments, relaxed
+    const F2 r11 = w[6] * (row4(E.F0, 2, d.S) - q.m11);
+    const F2 r12 = w[7] * row4(E.F0, 3, d.S);
+    const F2 r7 = w[2] * (row4(E.FX, 1, d.X) - q.m7);
+    const F2 r9 = w[4] * (row4(E.FX, 2, d.X) - q.m9);
+    const F2 r15 = w[10] * row4(E.FX, 3, d.X);
+    const F2 r8 = w[3] * (row4(E.FY, 1, d.Y) - q.m8);
+    const F2 r10 = w[5] * (row4(E.FY, 2, d.Y) - q.m10);
+    const F2 r16 = w[11] * row4(E.FY, 3, d.Y);
+    const F2 r5 = w[0] * (E.FC[0][0] * d.C[0] + E.FC[0][1] * d.C[1] - q.m5);
+    const F2 r13 = w[8] * (E.FC[1][0] * d.C[0] + E.FC[1][1] * d.C[1] - q.m13);
+    const F2 r6 = w[1] * (E.FS[0][0] * d.C[2] + E.FS[0][1] * d.C[3] - q.m6);
+    const F2 r14 = w[9] * (E.FS[1][0] * d.C[2] + E.FS[1][1] * d.C[3] - q.m14);
+    F2 S[4], C[4], X[4], Y[4], df[16];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        S[g] = A.E.E0[g][2] * r11 + A.E.E0[g][3] * r12;
-        X[g] = A.E.EX[g][1] * r7 + A.E.EX[g][2] * r9 + A.E.EX[g][3] * r15;
-        Y[g] = A.E.EY[g][1] * r8 + A.E.EY[g][2] * r10 + A.E.EY[g][3] * r16;
+    for (int g = 0; g < 4; ++g) {
+      S[g] = E.E0[g][2] * r11 + E.E0[g][3] * r12;
+      X[g] = E.EX[g][1] * r7 + E.EX[g][2] * r9 + E.EX[g][3] * r15;
+      Y[g] = E.EY[g][1] * r8 + E.EY[g][2] * r10 + E.EY[g][3] * r16;
+    }
+    C[0] = E.EC[0][0] * r5 + E.EC[0][1] * r13;
+    C[1] = E.EC[1][0] * r5 + E.EC[1][1] * r13;
+    C[2] = E.ES[0][0] * r6 + E.ES[0][1] * r14;
+    C[3] = E.ES[1][0] * r6 + E.ES[1][1] * r14;
+    inverse_transform(S, C, X, Y, df);
+    bad |= !(m.rho.v.x > 0.0f) || !isfinite(m.rho.v.x + m.jx.v.x + m.jy.v.x + m.e.v.x);
+    bad |= actb && (!(m.rho.v.y > 0.0f) || !isfinite(m.rho.v.y + m.jx.v.y + m.jy.v.y + m.e.v.y));
+    const bool wa = xa > 0, ea = xa < nx - 1, wb = xb > 0, eb = xb < nx - 1;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      F2 out;
+      if (xclass(i) == 0) {
+        out = f[i] + df[i];
+      } else {
+        const int g = xclass(i) - 1;
+        const float s = xsign(i);
+        const F2 fe(ea ? sa[i * W + 1] : gR[i], eb ? sb[i * W + 1] : gR[i]);
+        const F2 fw(wa ? sa[i * W - 1] : gL[i], wb ? sb[i * W - 1] : gL[i]);
+        out = (1.0f - 2.0f * be[g]) * f[i] + df[i];
+        out = (be[g] - s * al[g]) * fe + out;
+        out = (be[g] + s * al[g]) * fw + out;
       }
-      C[0] = A.E.EC[0][0] * r5 + A.E.EC[0][1] * r13;
-      C[1] = A.E.EC[1][0] * r5 + A.E.EC[1][1] * r13;
-      C[2] = A.E.ES[0][0] * r6 + A.E.ES[0][1] * r14;
-      C[3] = A.E.ES[1][0] * r6 + A.E.ES[1][1] * r14;
-      inverse_transform(S, C, X, Y, df);
-      bad |= !(m.rho > 0.0f) || !isfinite(m.rho + m.jx + m.jy + m.e);
-      const bool west = x > 0, east = x < nx - 1;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        float out;
-        if (xclass(i) == 0) {
-          out = f[i] + df[i];
-        } else {
-          const int g = xclass(i) - 1;
-          const float s = xsign(i);
-          const float fe = east ? fin[i * P + c + 1] : gR[i];
-          const float fw = west ? fin[i * P + c - 1] : gL[i];
-          out = (1.0f - 2.0f * be[g]) * f[i] + df[i];
-          out += (be[g] - s * al[g]) * fe;
-          out += (be[g] + s * al[g]) * fw;
-        }
-        fout[i * P + c] = out;
-      }
+      fout[i * P + off + xa] = out.v.x;
+      if (actb) fout[i * P + off + xb] = out.v.y;
     }
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
@@ -202,10 +239,16 @@ __device__ __forceinline__ void tube_tile(const BatchArgs& A, const float* __res
 template <int BT, int TILE>
 __global__ void __launch_bounds__(BT) k_tubes(float* f0, float* f1, const BatchArgs A,
                                               long long nsteps) {
+  extern __shared__ __align__(16) unsigned char tube_smem[];
+  float* const stages = reinterpret_cast<float*>(tube_smem);  // [2][16][stage_width]
+  constexpr int SE = 16 * stage_width<TILE>();
+  __shared__ unsigned long long bar[2];
   __shared__ unsigned long long s_level;
   __shared__ int s_cur;
   __shared__ unsigned s_gen;
   if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     s_level = *(volatile unsigned long long*)&A.st->step;
     s_cur = *(volatile int*)&A.st->cur;
     s_gen = *(volatile unsigned*)&A.st->bar_gen;
@@ -214,14 +257,39 @@ __global__ void __launch_bounds__(BT) k_tubes(float* f0, float* f1, const BatchA
   const unsigned long long level0 = s_level;
   const int cur = s_cur;
   unsigned gen = s_gen;
+  long long k = 0;  // items processed by this block: stage k & 1, phase (k >> 1) & 1
   // All blocks read the state above before anyone can pass this barrier.
   if (!grid_barrier(A, gen, false)) return;
   for (long long s = 0; s < nsteps; ++s) {
     const bool even = ((s + cur) & 1) == 0;
     const float* fin = even ? f0 : f1;
     float* fout = even ? f1 : f0;
-    for (int item = blockIdx.x; item < A.nitems; item += gridDim.x)
-      tube_tile<BT, TILE>(A, fin, fout, item, level0 + (unsigned long long)s);
+    // Plain stores of the previous step are read below by bulk copies.
+    fence_proxy_async();
+    if (threadIdx.x == 0 && (int)blockIdx.x < A.nitems)
+      issue_item<TILE>(A, fin, stages + (k & 1) * SE, blockIdx.x, &bar[k & 1]);
+    for (int item = blockIdx.x; item < A.nitems; item += gridDim.x, ++k) {
+      const int st = (int)(k & 1);
+      const int next = item + (int)gridDim.x;
+      // Stage 1 - st was released at the end of the previous item.
+      if (threadIdx.x == 0 && next < A.nitems)
+        issue_item<TILE>(A, fin, stages + (1 - st) * SE, next, &bar[1 - st]);
+      if (!__syncthreads_and(mbar_wait_bounded(&bar[st], (unsigned)((k >> 1) & 1), TMA_WAIT_CYCLES))) {
+        // A copy did not land: record it (the other blocks leave at the next
+        // barrier), wait once more for this block's copies, leave.
+        if (threadIdx.x == 0) {
+          atomicExch(&A.st->timeout, 1);
+          atomicMin(&A.st->first_timeout_step, level0 + s);
+          mbar_wait_bounded(&bar[st], (unsigned)((k >> 1) & 1), TMA_WAIT_CYCLES);
+          if (next < A.nitems)
+            mbar_wait_bounded(&bar[1 - st], (unsigned)(((k + 1) >> 1) & 1), TMA_WAIT_CYCLES);
+        }
+        return;
+      }
+      tube_item<BT, TILE>(A, fout, stages + st * SE, item, level0 + (unsigned long long)s);
+      __syncthreads();  // stage st is free again
+    }
+    fence_proxy_async();
     const bool skip = (int)blockIdx.x == A.skip_block && s == A.skip_step;
     if (!grid_barrier(A, gen, skip)) {
       if (threadIdx.x == 0) atomicMin(&A.st->first_timeout_step, level0 + s);
@@ -328,11 +396,14 @@ struct Variant {
   KernelFn fn;
 };
 const Variant VARIANTS[] = {
-    {64, 64, k_tubes<64, 64>},       {128, 64, k_tubes<64, 128>},
-    {128, 128, k_tubes<128, 128>},   {256, 128, k_tubes<128, 256>},
-    {512, 128, k_tubes<128, 512>},   {256, 256, k_tubes<256, 256>},
+    {128, 64, k_tubes<64, 128>},     {256, 64, k_tubes<64, 256>},
+    {256, 128, k_tubes<128, 256>},   {512, 128, k_tubes<128, 512>},
     {512, 256, k_tubes<256, 512>},   {1024, 256, k_tubes<256, 1024>},
+    {1024, 512, k_tubes<512, 1024>}, {1024, 128, k_tubes<128, 1024>},
 };
+size_t variant_smem(int v) {
+  return 2 * 16 * sizeof(float) * (size_t)(VARIANTS[v].tile + 8) + 16;
+}
 constexpr int NVARIANTS = sizeof(VARIANTS) / sizeof(VARIANTS[0]);
 
 int find_variant(int tile, int threads) {
@@ -463,7 +534,10 @@ int build_items(lbm_batch* b) {
                          cudaMemcpyHostToDevice, b->stream));
   int per_sm = 0;
   const Variant& V = VARIANTS[b->variant];
-  BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.fn, V.threads, 0));
+  const size_t smem = variant_smem(b->variant);
+  BCK(b, cudaFuncSetAttribute((const void*)V.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem));
+  BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.fn, V.threads, smem));
   if (per_sm < 1) return bfail(b, LBM_ERR_CUDA, "tube kernel does not fit on an SM");
   b->blocks = std::min(per_sm * b->sms, b->nitems);
   for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
@@ -499,6 +573,7 @@ int launch_tubes(lbm_batch* b, long long nsteps) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->blocks);
   cfg.blockDim = dim3(V.threads);
+  cfg.dynamicSmemBytes = variant_smem(b->variant);
   cfg.stream = b->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -559,7 +634,7 @@ int lbm_batch_create(const lbm_batch_config* cfg, void* cuda_stream, lbm_batch**
     delete b;
     return bfail(nullptr, LBM_ERR_INVALID, "singular moment block");
   }
-  long long off = 0, outo = 0;
+  long long off = TUBE_PAD, outo = 0;
   for (int t = 0; t < b->ntubes; ++t) {
     TubeDesc D;
     D.off = off;
@@ -571,7 +646,7 @@ int lbm_batch_create(const lbm_batch_config* cfg, void* cuda_stream, lbm_batch**
     off += (D.nx + 31) / 32 * 32;
     outo += D.nx;
   }
-  b->plane = off;
+  b->plane = off + TUBE_PAD;
   b->total = outo;
   cudaError_t e = cudaSuccess;
   int dev = 0, clk_khz = 0;
