@@ -73,13 +73,18 @@ enum lbm_precision {
  *            the next one inwards; q1 if that has rho <= 0 or T <= 0
  *            (linear extrapolation, Sec. V.B.a and V.C);
  *  WALL      (rho of the adjacent node, bc.u, bc.v, bc.T): a moving wall at
- *            fixed temperature (Couette flow, Sec. V.D). */
+ *            fixed temperature (Couette flow, Sec. V.D);
+ *  OUTFLOW   the adjacent interior node unchanged (zero-gradient, free
+ *            outflow; not used in the paper: open sides of 2D Riemann
+ *            problems, where linear extrapolation amplifies waves that
+ *            cross the side). */
 enum lbm_bc_kind {
   LBM_BC_PERIODIC = 0,
   LBM_BC_EQ = 1,
   LBM_BC_REFLECT = 2,
   LBM_BC_EXTRAP = 3,
-  LBM_BC_WALL = 4
+  LBM_BC_WALL = 4,
+  LBM_BC_OUTFLOW = 5
 };
 
 typedef struct {

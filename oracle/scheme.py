@@ -38,6 +38,10 @@ R7  Extrapolating side: ghost q = 2 q_1 - q_2 for q in (rho, u, v, T), q_1 the
 R8  Moving isothermal wall (Couette, Sec. V.D: "constant speed and constant
     temperature"): the ghost state is (rho of the adjacent node, u_w, v_w,
     T_w); the paper does not say what density the wall node carries.
+R20 Open side of problems the paper does not pose (2D Riemann quadrants):
+    zero-gradient outflow, the ghost state is the adjacent node's state
+    (zero-order extrapolation; the first-order one of R7 amplifies waves that
+    cross such a side).
 """
 import numpy as np
 
@@ -169,6 +173,9 @@ def _ghost_line(f, side, bc):
         q1 = list(macroscopic(first))
         q2 = list(macroscopic(second))
         return equilibrium_populations(*_extrapolate(q1, q2))
+    if kind == "outflow":
+        # zero-gradient open side: the adjacent node's state unchanged
+        return equilibrium_populations(*macroscopic(first))
     if kind == "wall":
         rho = macroscopic(first)[0]
         _, uw, vw, Tw = (float(x) for x in state)

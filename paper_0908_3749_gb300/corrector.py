@@ -140,3 +140,64 @@ def evaluate(net, pairs, mass_tol=1e-2):
     n = max(len(pairs), 1)
     return {"plain": np.mean(plain, axis=0).tolist(), "corrected": np.mean(corr, axis=0).tolist(),
             "fallbacks": fallbacks, "inference_s_per_problem": t_inf / n}
+
+
+def main(argv=None):
+    """Full-size evaluation: trains on seeded quadrant problems and reports,
+    on held-out seeds, the error of the plain and of the corrected coarse run
+    against the restricted fine run, and the wall time of the fine run
+    against the coarse run plus inference. One JSON line.
+
+        python -m paper_0908_3749_gb300.corrector --n 512 --ratio 4 --t-end 0.02
+    """
+    import argparse
+    import json
+
+    import workloads as W
+    ap = argparse.ArgumentParser(description="learned coarse-grid corrector: train and evaluate")
+    ap.add_argument("--n", type=int, default=512, help="coarse grid n x n")
+    ap.add_argument("--ratio", type=int, default=4, help="fine / coarse resolution")
+    ap.add_argument("--t-end", type=float, default=0.02)
+    ap.add_argument("--dt", type=float, default=1e-5, help="coarse time step (fine: dt / ratio)")
+    ap.add_argument("--train", type=int, default=24, help="training seeds 1 .. train")
+    ap.add_argument("--test", type=int, default=8, help="held-out seeds 10001 .. 10000 + test")
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    args = ap.parse_args(argv)
+
+    t0 = time.perf_counter()
+    train_pairs, skipped_tr, tm_tr = make_pairs(W.corrector_quadrant, range(1, args.train + 1),
+                                                args.n, args.ratio, args.t_end, args.dt)
+    test_pairs, skipped_te, tm_te = make_pairs(W.corrector_quadrant,
+                                               range(10001, 10001 + args.test),
+                                               args.n, args.ratio, args.t_end, args.dt)
+    t1 = time.perf_counter()
+    if not train_pairs or not test_pairs:
+        raise SystemExit("every problem was rejected")
+    net, losses = train(train_pairs, epochs=args.epochs, lr=args.lr, seed=0)
+    t2 = time.perf_counter()
+    try:
+        res = evaluate(net, test_pairs)
+    finally:
+        lbm.lbm_cnn_destroy(net)
+    coarse_s = tm_te["coarse_s_per_problem"]
+    fine_s = tm_te["fine_s_per_problem"]
+    out = {
+        "workload": "2D Riemann quadrants, coarse %dx%d, fine %dx%d, t_end %g"
+                    % (args.n, args.n, args.n * args.ratio, args.n * args.ratio, args.t_end),
+        "train_problems": len(train_pairs), "train_rejected": skipped_tr,
+        "test_problems": len(test_pairs), "test_rejected": skipped_te,
+        "rel_l1_plain": dict(zip(("rho", "u", "v", "T"), res["plain"])),
+        "rel_l1_corrected": dict(zip(("rho", "u", "v", "T"), res["corrected"])),
+        "fallbacks": res["fallbacks"],
+        "fine_run_s": fine_s, "coarse_run_s": coarse_s,
+        "inference_s": res["inference_s_per_problem"],
+        "speedup_vs_fine": fine_s / (coarse_s + res["inference_s_per_problem"]),
+        "loss_first_last": [losses[0], losses[-1]], "epochs": args.epochs,
+        "data_s": t1 - t0, "train_s": t2 - t1,
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

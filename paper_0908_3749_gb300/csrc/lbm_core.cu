@@ -743,7 +743,7 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
   if (C.audit_every < 0) return fail(nullptr, LBM_ERR_INVALID, "audit_every < 0");
   for (int s = 0; s < 4; ++s) {
     const lbm_bc& b = C.bc[s];
-    if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_WALL)
+    if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_OUTFLOW)
       return fail(nullptr, LBM_ERR_INVALID, "bad boundary kind");
     if (b.kind == LBM_BC_EQ && !(finite_pos(b.rho) && finite_pos(b.T) &&
                                  std::isfinite(b.u) && std::isfinite(b.v)))

@@ -170,6 +170,8 @@ __device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict_
     s.jx = own.rho * u;
     s.jy = own.rho * v;
     s.e = own.rho * T + R(0.5) * own.rho * (u * u + v * v);
+  } else if (kind == LBM_BC_OUTFLOW) {
+    // the adjacent node's state unchanged
   } else {  // LBM_BC_EXTRAP
     const Cons<R> in = has_inward ? load_cons(A.K, fin, plane, inward) : own;
     const R r1 = recip(own.rho), r2 = recip(in.rho);

@@ -26,7 +26,7 @@ LBM_ERR_TIMEOUT = -6
 LBM_FP64, LBM_FP32, LBM_TC_BF16X3, LBM_TC_TF32X3 = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "tc_bf16x3": LBM_TC_BF16X3,
               "tc_tf32x3": LBM_TC_TF32X3}
-BC = {"periodic": 0, "eq": 1, "reflect": 2, "extrap": 3, "wall": 4}
+BC = {"periodic": 0, "eq": 1, "reflect": 2, "extrap": 3, "wall": 4, "outflow": 5}
 AUDIT_RING = 1024
 
 

@@ -37,6 +37,8 @@ BC_SETS = [
     (("extrap", None), ("extrap", None), ("wall", (1.0, -0.1, 0.0, 1.0)), ("wall", (1.0, 0.1, 0.0, 1.0))),
     (("eq", (1.0, 0.3, 0.0, 1.0)), ("extrap", None), ("reflect", None), ("eq", (1.2, 0.25, -0.1, 1.1))),
     (("reflect", None), ("wall", (1.0, 0.0, 0.2, 1.3)), ("extrap", None), ("reflect", None)),
+    (("outflow", None), ("outflow", None), ("outflow", None), ("outflow", None)),
+    (("outflow", None), ("eq", (1.1, 0.2, 0.0, 0.9)), ("reflect", None), ("outflow", None)),
 ]
 
 

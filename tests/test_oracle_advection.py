@@ -101,6 +101,35 @@ def test_ghost_states():
     np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
 
 
+def test_outflow_ghost_agrees_with_reflect_and_extrap_where_they_coincide():
+    """Zero-gradient outflow (reading R20) against the two other kinds built
+    from the adjacent node: equal to the reflecting ghost where the normal
+    velocity is zero, and to the extrapolating one where the first two
+    interior lines are equal."""
+    w = W.random_state(6, 5, seed=31)
+    rho, u, v, T = (np.array(a, dtype=np.float64) for a in w.fields())
+    v[0, :] = 0.0                                  # no normal velocity on row 0
+    f = scheme.init_populations(rho, u, v, T)
+    np.testing.assert_allclose(scheme._ghost_line(f, "y-", ("outflow", None)),
+                               scheme._ghost_line(f, "y-", ("reflect", None)), rtol=0, atol=1e-14)
+    rho2, u2, v2, T2 = (a.copy() for a in (rho, u, v, T))
+    for q in (rho2, u2, v2, T2):
+        q[:, 1] = q[:, 0]                          # columns 0 and 1 equal
+    f2 = scheme.init_populations(rho2, u2, v2, T2)
+    np.testing.assert_allclose(scheme._ghost_line(f2, "x-", ("outflow", None)),
+                               scheme._ghost_line(f2, "x-", ("extrap", None)), rtol=1e-12, atol=1e-13)
+
+
+def test_uniform_state_is_fixed_with_outflow_sides():
+    n = (7, 5)
+    st = (1.3, 0.2, -0.1, 0.8)
+    f = scheme.init_populations(*(np.full(n[::-1], x) for x in st))
+    bc = (("outflow", None),) * 4
+    w = W.random_state(n[0], n[1], seed=1, bc=bc)
+    out = scheme.step(f, w.cfg())
+    np.testing.assert_allclose(out, f, rtol=1e-12, atol=1e-13)
+
+
 def test_extrapolation_falls_back_when_unphysical():
     rho = np.array([[0.2, 1.0]])
     T = np.array([[1.0, 1.0]])
