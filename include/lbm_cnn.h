@@ -7,8 +7,11 @@
  * (log rho, u, v, log T) of a coarse MRT-FD run to a correction of the same
  * features: corrected = features + net(features). It is trained to match the
  * restriction (block means of rho, j, e) of a finer run of the same method.
- * Weights are stored in FP32 (Adam master copy) and used in BF16 by the
- * tensor-core convolutions, which accumulate in FP32.
+ * Weights are stored in FP32 (Adam master copy). The first layer reads the
+ * FP32 features and runs in FP32 (so that differences between neighbouring
+ * nodes below one BF16 step are seen); the other layers use BF16 weights and
+ * activations in tensor-core convolutions that accumulate in FP32, and the
+ * correction is added to the FP32 features.
  *
  * Fields are 4 planes [4][H][W] (rho, u, v, T), FP64, row-major, x fastest.
  * Parameters are packed per layer as w[3][3][cin][cout] then b[cout], FP32,
@@ -38,7 +41,8 @@ int lbm_cnn_set_params(lbm_cnn* n, const float* params, int on_device);
 int lbm_cnn_get_params(lbm_cnn* n, float* params, int on_device);
 int lbm_cnn_set_adam(lbm_cnn* n, double lr, double beta1, double beta2, double eps);
 
-/* Loss (mean squared feature error against the target fields) and the
+/* Loss (mean squared or absolute feature error against the target fields,
+ * lbm_cnn_set_loss) and the
  * gradient of every parameter (packed, FP32) for one coarse / target pair,
  * without updating. Fields: device pointers [4][H][W]. *loss and grads are
  * host outputs; synchronises. */
@@ -50,6 +54,27 @@ int lbm_cnn_loss_grad(lbm_cnn* n, const double* coarse, const double* target,
  * update and synchronises when requested. */
 int lbm_cnn_train_step(lbm_cnn* n, const double* coarse, const double* target,
                        double* loss);
+
+/* Training loss over the features of out = corrected, t = target, N values:
+ * LBM_CNN_LOSS_MSE sum (out - t)^2 / N (default), LBM_CNN_LOSS_L1
+ * sum |out - t| / N (the paper's error measure E of Sec. V.A is a relative
+ * L1 norm). */
+#define LBM_CNN_LOSS_MSE 0
+#define LBM_CNN_LOSS_L1 1
+int lbm_cnn_set_loss(lbm_cnn* n, int kind);
+
+/* Output scale: the network predicts the correction of feature c (log rho,
+ * u, v, log T) in units of scale[c] (corrected = features + scale * net),
+ * host array of 4 values > 0; default 1. Setting it to the RMS correction
+ * of the training data keeps the network's outputs of order one, so that
+ * the rounding noise of its BF16 layers is a small fraction of the
+ * corrections it has to produce. */
+int lbm_cnn_set_output_scale(lbm_cnn* n, const double* scale);
+
+/* rms[c] (host, 4 values) = root mean square over the image of the
+ * difference target - coarse of feature c. Device fields [4][H][W].
+ * Synchronises. */
+int lbm_cnn_residual_rms(lbm_cnn* n, const double* coarse, const double* target, double* rms);
 
 /* Corrected fields [4][H][W] (device) from coarse fields (device). Falls back
  * to the plain coarse fields when the corrected total mass differs from the

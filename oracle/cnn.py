@@ -52,11 +52,14 @@ def bf16(a):
     return r.view(np.float32).astype(np.float64)
 
 
-def forward(x, params, x_res=None, store=None):
-    """params: list of (w, b). Returns (out, cache); out = x_res + net(x)
-    with x_res = x unless given (the network may see a rounded copy of the
-    features while the residual adds the unrounded ones)."""
+def forward(x, params, x_res=None, store=None, scale=None):
+    """params: list of (w, b). Returns (out, cache); out = x_res + scale *
+    net(x) with x_res = x unless given (the network may see a rounded copy of
+    the features while the residual adds the unrounded ones) and scale a
+    per-channel factor (default 1): the network predicts the correction in
+    units of ``scale``."""
     store = store or (lambda a: a)
+    scale = np.ones(x.shape[-1]) if scale is None else np.asarray(scale, dtype=np.float64)
     acts = [x]
     pres = []
     h = x
@@ -66,18 +69,26 @@ def forward(x, params, x_res=None, store=None):
         pres.append(z)
         h = store(np.maximum(z, 0.0)) if l < L - 1 else z
         acts.append(h)
-    return (x if x_res is None else x_res) + h, (acts, pres)
+    return (x if x_res is None else x_res) + scale * h, (acts, pres)
 
 
-def loss_and_grads(x, target, params, x_res=None, store=None):
+def loss_and_grads(x, target, params, x_res=None, store=None, scale=None, loss="mse"):
     """Loss and per-layer (dw, db). ``store`` (default: identity) is applied
     wherever a mixed-precision pipeline stores a value: the hidden
-    activations and the gradient flowing into each layer's output."""
-    out, (acts, pres) = forward(x, params, x_res, store)
+    activations and the gradient flowing into each layer's output. ``loss``:
+    "mse" (mean of (out - target)^2) or "l1" (mean of |out - target|, with
+    the subgradient sign(out - target), 0 where they are equal)."""
+    out, (acts, pres) = forward(x, params, x_res, store, scale)
     store = store or (lambda a: a)
+    scale = np.ones(x.shape[-1]) if scale is None else np.asarray(scale, dtype=np.float64)
     n = out.size
-    loss = float(((out - target) ** 2).sum() / n)
-    g = store(2.0 * (out - target) / n)   # d loss / d out = d loss / d net
+    d = out - target
+    if loss == "l1":
+        value = float(np.abs(d).sum() / n)
+        g = store(scale * np.sign(d) / n)    # d loss / d net (chain rule through scale)
+    else:
+        value = float((d ** 2).sum() / n)
+        g = store(2.0 * scale * d / n)
     grads = [None] * len(params)
     for l in range(len(params) - 1, -1, -1):
         w, _ = params[l]
@@ -86,7 +97,7 @@ def loss_and_grads(x, target, params, x_res=None, store=None):
         dx, dw, db = conv3x3_backward(acts[l], w, g)
         grads[l] = (dw, db)
         g = dx
-    return loss, grads
+    return value, grads
 
 
 def restrict(rho, u, v, T, r):

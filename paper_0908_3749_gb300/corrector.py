@@ -95,13 +95,23 @@ def init_params(seed):
     return p
 
 
-def train(pairs, epochs=20, lr=1e-3, seed=0, stream=None, log_every=0):
-    """Trains a fresh network on ``pairs``; returns (handle, losses).
-    The caller owns the handle (lbm.lbm_cnn_destroy)."""
+def train(pairs, epochs=20, lr=1e-3, seed=0, stream=None, log_every=0, loss="l1"):
+    """Trains a fresh network on ``pairs``; returns (handle, losses). The
+    loss is "l1" (mean absolute feature error, the measure the evaluation
+    reports) or "mse"; the network's output scale is the RMS correction
+    (restricted fine minus coarse) of each feature over the pairs. The
+    caller owns the handle (lbm.lbm_cnn_destroy)."""
     H, W = pairs[0][0].shape[1:]
     net = lbm.lbm_cnn_create(H, W, stream)
     lbm.lbm_cnn_set_params(net, init_params(seed))
     lbm.lbm_cnn_set_adam(net, lr)
+    lbm.lbm_cnn_set_loss(net, loss)
+    # Corrections in units of the training data's RMS correction per feature.
+    ms = np.zeros(4)
+    for c, t in pairs:
+        ms += np.square(lbm.lbm_cnn_residual_rms(net, c, t))
+    scale = np.sqrt(ms / len(pairs))
+    lbm.lbm_cnn_set_output_scale(net, np.where(scale > 0, scale, 1.0))
     rng = np.random.default_rng(seed + 1)
     losses = []
     for ep in range(epochs):
@@ -121,12 +131,17 @@ def rel_l1(a, b):
     return [float((a[k] - b[k]).abs().sum() / b[k].abs().sum()) for k in range(4)]
 
 
+def rel_l2(a, b):
+    """Per field: sqrt(sum (a - b)^2 / sum b^2) over the grid."""
+    return [float(((a[k] - b[k]) ** 2).sum().sqrt() / (b[k] ** 2).sum().sqrt()) for k in range(4)]
+
+
 def evaluate(net, pairs, mass_tol=1e-2):
     """Mean relative L1 error per field (rho, u, v, T) of the plain coarse
     fields and of the corrected ones against the restricted fine fields, the
     number of fallbacks, and the inference time per problem."""
     import torch
-    plain, corr, fallbacks, t_inf = [], [], 0, 0.0
+    plain, corr, plain2, corr2, fallbacks, t_inf = [], [], [], [], 0, 0.0
     for coarse, target in pairs:
         out = torch.empty_like(coarse)
         torch.cuda.synchronize()
@@ -137,8 +152,12 @@ def evaluate(net, pairs, mass_tol=1e-2):
         fallbacks += int(fb)
         plain.append(rel_l1(coarse, target))
         corr.append(rel_l1(out, target))
+        plain2.append(rel_l2(coarse, target))
+        corr2.append(rel_l2(out, target))
     n = max(len(pairs), 1)
     return {"plain": np.mean(plain, axis=0).tolist(), "corrected": np.mean(corr, axis=0).tolist(),
+            "plain_l2": np.mean(plain2, axis=0).tolist(),
+            "corrected_l2": np.mean(corr2, axis=0).tolist(),
             "fallbacks": fallbacks, "inference_s_per_problem": t_inf / n}
 
 
@@ -163,6 +182,7 @@ def main(argv=None):
     ap.add_argument("--test", type=int, default=8, help="held-out seeds 10001 .. 10000 + test")
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--loss", choices=("l1", "mse"), default="l1")
     args = ap.parse_args(argv)
 
     t0 = time.perf_counter()
@@ -174,7 +194,7 @@ def main(argv=None):
     t1 = time.perf_counter()
     if not train_pairs or not test_pairs:
         raise SystemExit("every problem was rejected")
-    net, losses = train(train_pairs, epochs=args.epochs, lr=args.lr, seed=0)
+    net, losses = train(train_pairs, epochs=args.epochs, lr=args.lr, seed=0, loss=args.loss)
     t2 = time.perf_counter()
     try:
         res = evaluate(net, test_pairs)
@@ -189,11 +209,13 @@ def main(argv=None):
         "test_problems": len(test_pairs), "test_rejected": skipped_te,
         "rel_l1_plain": dict(zip(("rho", "u", "v", "T"), res["plain"])),
         "rel_l1_corrected": dict(zip(("rho", "u", "v", "T"), res["corrected"])),
+        "rel_l2_plain": dict(zip(("rho", "u", "v", "T"), res["plain_l2"])),
+        "rel_l2_corrected": dict(zip(("rho", "u", "v", "T"), res["corrected_l2"])),
         "fallbacks": res["fallbacks"],
         "fine_run_s": fine_s, "coarse_run_s": coarse_s,
         "inference_s": res["inference_s_per_problem"],
         "speedup_vs_fine": fine_s / (coarse_s + res["inference_s_per_problem"]),
-        "loss_first_last": [losses[0], losses[-1]], "epochs": args.epochs,
+        "loss": args.loss, "loss_first_last": [losses[0], losses[-1]], "epochs": args.epochs,
         "data_s": t1 - t0, "train_s": t2 - t1,
     }
     print(json.dumps(out))

@@ -1,8 +1,9 @@
 // lbm_cnn.cu -- training and inference kernels of the coarse-grid corrector
 // (include/lbm_cnn.h).
 //
-// Activations are BF16, pixel-major (NHWC, one image): a[p][c], p = y W + x.
-// 3 x 3 convolutions are implicit GEMMs on the tensor cores
+// Activations are BF16, pixel-major (NHWC, one image): a[p][c], p = y W + x;
+// the input features stay FP32 and the first layer (4 -> 32) runs in FP32 on
+// the CUDA cores. The other 3 x 3 convolutions are implicit GEMMs on the tensor cores
 // (mma.sync m16n8k16, BF16 inputs, FP32 accumulation): rows are pixels, the
 // reduction index k = tap * CIN + ci runs over the 9 taps and the input
 // channels, columns are output channels. The weights of a layer are packed
@@ -138,8 +139,11 @@ __global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16* __restrict__ 
 // dW[tap][ci][co] = sum_p act[p + off(tap)][ci] dz[p][co]; thread 9 CIN + co
 // (co < COUT) owns db[co] = sum_p dz[p][co]. Block b sums pixels
 // [b * chunk, (b + 1) * chunk).
-template <int CIN, int COUT>
-__global__ void k_wgrad(const __nv_bfloat16* __restrict__ act, const __nv_bfloat16* __restrict__ dz,
+__device__ __forceinline__ float to_f32(float a) { return a; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 a) { return __bfloat162float(a); }
+
+template <int CIN, int COUT, typename TA>
+__global__ void k_wgrad(const TA* __restrict__ act, const __nv_bfloat16* __restrict__ dz,
                         int H, int W, int chunk, float* __restrict__ partial) {
   const int t = threadIdx.x;
   constexpr int NW = 9 * CIN * COUT, NOUT = NW + COUT;
@@ -158,7 +162,7 @@ __global__ void k_wgrad(const __nv_bfloat16* __restrict__ act, const __nv_bfloat
       const int yy = y + dy, xx = x + dx;
       float a = 0.f;
       if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-        a = __bfloat162float(act[((long long)yy * W + xx) * CIN + ci]);
+        a = to_f32(act[((long long)yy * W + xx) * CIN + ci]);
 #pragma unroll
       for (int c = 0; c < COUT; ++c) acc[c] += a * __bfloat162float(dz[(long long)p * COUT + c]);
     } else if (bthread) {
@@ -172,6 +176,43 @@ __global__ void k_wgrad(const __nv_bfloat16* __restrict__ act, const __nv_bfloat
   } else if (bthread) {
     out[NW + (t - 9 * CIN)] = acc[0];
   }
+}
+
+// First layer (4 -> 32 channels) in FP32 on the CUDA cores, straight from the
+// FP32 input features [p][4]: 3 x 3 correlation with zero padding, bias,
+// ReLU, stored BF16 [p][32] for the tensor-core layers. Keeping the input in
+// FP32 keeps differences between neighbouring nodes that are below one BF16
+// step of the fields (smooth regions of fine-grained coarse grids).
+// w: the layer's FP32 parameters, (3, 3, 4, 32) then 32 biases.
+constexpr int C0_T = 128;
+__global__ void __launch_bounds__(C0_T) k_conv0(const float* __restrict__ xf, int H, int W,
+                                                const float* __restrict__ w,
+                                                __nv_bfloat16* __restrict__ out) {
+  __shared__ float sw[9 * 4 * 32 + 32];
+  for (int i = threadIdx.x; i < 9 * 4 * 32 + 32; i += C0_T) sw[i] = w[i];
+  __syncthreads();
+  const int p = blockIdx.x * C0_T + threadIdx.x;
+  if (p >= H * W) return;
+  const int y = p / W, x = p - y * W;
+  float acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = sw[9 * 4 * 32 + c];
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+    const float4 q = *reinterpret_cast<const float4*>(xf + 4 * ((long long)yy * W + xx));
+    const float qi[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci)
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c] += qi[ci] * sw[(tap * 4 + ci) * 32 + c];
+  }
+  __nv_bfloat16* o = out + (long long)p * 32;
+#pragma unroll
+  for (int c = 0; c < 32; c += 2)
+    *reinterpret_cast<__nv_bfloat162*>(o + c) =
+        __floats2bfloat162_rn(fmaxf(acc[c], 0.f), fmaxf(acc[c + 1], 0.f));
 }
 
 // grad[i] = sum over blocks b (in order) of partial[b][i].
@@ -189,30 +230,41 @@ __global__ void k_sum_partials(const float* __restrict__ partial, int nblocks, i
 // ---------------------------------------------------------------------------
 // Planes [4][H][W] (rho, u, v, T) -> features (log rho, u, v, log T) in FP32
 // [p][4] and BF16 [p][4].
-__global__ void k_features(const double* __restrict__ f, int npix, float* __restrict__ xf,
-                           __nv_bfloat16* __restrict__ xb) {
+__global__ void k_features(const double* __restrict__ f, int npix, float* __restrict__ xf) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npix) return;
-  const float q[4] = {(float)log(f[p]), (float)f[npix + p], (float)f[2 * npix + p],
-                      (float)log(f[3 * npix + p])};
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    if (xf) xf[4 * p + c] = q[c];
-    if (xb) xb[4 * p + c] = __float2bfloat16(q[c]);
-  }
+  xf[4 * p] = (float)log(f[p]);
+  xf[4 * p + 1] = (float)f[npix + p];
+  xf[4 * p + 2] = (float)f[2 * npix + p];
+  xf[4 * p + 3] = (float)log(f[3 * npix + p]);
 }
 
 // out = x + z; d = out - target; dz = 2 d / N (BF16); block partial of sum d^2.
+// Per-channel output scale: the network predicts the correction of feature
+// c in units of s[c] (out = x + s z).
+struct Scale4 {
+  float s[4];
+};
+
+// Loss per element of out - target, d: d^2 (LBM_CNN_LOSS_MSE) or |d|
+// (LBM_CNN_LOSS_L1, whose gradient is sign(d), 0 at d = 0); summed per block.
 __global__ void k_loss(const float* __restrict__ xf, const float* __restrict__ z,
                        const float* __restrict__ tf, int n, __nv_bfloat16* __restrict__ dz,
-                       double* __restrict__ partial) {
+                       double* __restrict__ partial, const Scale4 sc, int l1) {
   __shared__ double sm[256];
   const int i = blockIdx.x * 256 + threadIdx.x;
   double s = 0.0;
   if (i < n) {
-    const float d = xf[i] + z[i] - tf[i];
-    s = (double)d * d;
-    if (dz) dz[i] = __float2bfloat16(2.f * d / (float)n);
+    const float k = sc.s[i & 3];
+    const float d = xf[i] + k * z[i] - tf[i];
+    if (l1) {
+      s = fabs((double)d);
+      const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+      if (dz) dz[i] = __float2bfloat16(k * sg / (float)n);
+    } else {
+      s = (double)d * d;
+      if (dz) dz[i] = __float2bfloat16(2.f * k * d / (float)n);
+    }
   }
   sm[threadIdx.x] = s;
   __syncthreads();
@@ -274,13 +326,14 @@ __global__ void k_pack(const float* __restrict__ w, int cin, int cout, int kp, i
 // corrected planes from output features x + z; block partial sums of rho.
 __global__ void k_apply(const float* __restrict__ xf, const float* __restrict__ z, int npix,
                         double* __restrict__ out, const double* __restrict__ coarse,
-                        double* __restrict__ partial) {
+                        double* __restrict__ partial, const Scale4 sc) {
   __shared__ double sm[2][256];
   const int p = blockIdx.x * 256 + threadIdx.x;
   double r = 0.0, r0 = 0.0;
   if (p < npix) {
-    const float q0 = xf[4 * p] + z[4 * p], q1 = xf[4 * p + 1] + z[4 * p + 1];
-    const float q2 = xf[4 * p + 2] + z[4 * p + 2], q3 = xf[4 * p + 3] + z[4 * p + 3];
+    const float q0 = xf[4 * p] + sc.s[0] * z[4 * p], q1 = xf[4 * p + 1] + sc.s[1] * z[4 * p + 1];
+    const float q2 = xf[4 * p + 2] + sc.s[2] * z[4 * p + 2];
+    const float q3 = xf[4 * p + 3] + sc.s[3] * z[4 * p + 3];
     r = exp((double)q0);
     out[p] = r;
     out[npix + p] = q1;
@@ -303,6 +356,26 @@ __global__ void k_apply(const float* __restrict__ xf, const float* __restrict__ 
     partial[2 * blockIdx.x] = sm[0][0];
     partial[2 * blockIdx.x + 1] = sm[1][0];
   }
+}
+
+// Block partial sums of (t - x)^2 per feature channel, [block][4].
+__global__ void k_residual_sq(const float* __restrict__ xf, const float* __restrict__ tf, int npix,
+                              double* __restrict__ partial) {
+  __shared__ double sm[4][256];
+  const int p = blockIdx.x * 256 + threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double d = p < npix ? (double)tf[4 * p + c] - (double)xf[4 * p + c] : 0.0;
+    sm[c][threadIdx.x] = d * d;
+  }
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sm[c][threadIdx.x] += sm[c][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) partial[4 * blockIdx.x + threadIdx.x] = sm[threadIdx.x][0];
 }
 
 __global__ void k_restrict(const double* __restrict__ f, int Hf, int Wf, int r,
@@ -346,7 +419,7 @@ struct lbm_cnn {
   float* grad = nullptr;
   __nv_bfloat16* wt[NL] = {};
   __nv_bfloat16* wb[NL] = {};
-  __nv_bfloat16* act[NL] = {};  // act[0] = input features, act[l] = relu output of layer l-1
+  __nv_bfloat16* act[NL] = {};  // act[l] = relu output of layer l-1 (act[0] unused)
   __nv_bfloat16* dz[2] = {};    // ping-pong output gradients
   float* xf = nullptr;          // input features FP32 [p][4]
   float* tf = nullptr;          // target features FP32 [p][4]
@@ -357,6 +430,8 @@ struct lbm_cnn {
   int wchunk = 0, wblocks = 0;
   long long step = 0;
   float lr = 1e-3f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  Scale4 scale = {{1.f, 1.f, 1.f, 1.f}};
+  int loss_kind = LBM_CNN_LOSS_MSE;
   std::string err = "no error";
 };
 
@@ -397,9 +472,10 @@ void conv(lbm_cnn* n, const __nv_bfloat16* in, const __nv_bfloat16* wt, const fl
 }
 
 int forward(lbm_cnn* n, const double* coarse) {
-  k_features<<<(n->npix + 255) / 256, 256, 0, n->stream>>>(coarse, n->npix, n->xf, n->act[0]);
+  k_features<<<(n->npix + 255) / 256, 256, 0, n->stream>>>(coarse, n->npix, n->xf);
   const float* w = n->w;
-  conv<4, 32, EPI_RELU_BF16>(n, n->act[0], n->wt[0], w + param_offset(0) + wsize(0), nullptr, n->act[1], nullptr);
+  k_conv0<<<(n->npix + C0_T - 1) / C0_T, C0_T, 0, n->stream>>>(n->xf, n->H, n->W,
+                                                               w + param_offset(0), n->act[1]);
   conv<32, 32, EPI_RELU_BF16>(n, n->act[1], n->wt[1], w + param_offset(1) + wsize(1), nullptr, n->act[2], nullptr);
   conv<32, 32, EPI_RELU_BF16>(n, n->act[2], n->wt[2], w + param_offset(2) + wsize(2), nullptr, n->act[3], nullptr);
   conv<32, 32, EPI_RELU_BF16>(n, n->act[3], n->wt[3], w + param_offset(3) + wsize(3), nullptr, n->act[4], nullptr);
@@ -408,20 +484,21 @@ int forward(lbm_cnn* n, const double* coarse) {
   return LBM_OK;
 }
 
-template <int CIN, int COUT>
-void wgrad(lbm_cnn* n, const __nv_bfloat16* act, const __nv_bfloat16* dzl, float* grad) {
+template <int CIN, int COUT, typename TA>
+void wgrad(lbm_cnn* n, const TA* act, const __nv_bfloat16* dzl, float* grad) {
   constexpr int NOUT = 9 * CIN * COUT + COUT;
   const int threads = ru(9 * CIN + COUT, 32);
-  k_wgrad<CIN, COUT><<<n->wblocks, threads, 0, n->stream>>>(act, dzl, n->H, n->W, n->wchunk,
-                                                             n->wpartial);
+  k_wgrad<CIN, COUT, TA><<<n->wblocks, threads, 0, n->stream>>>(act, dzl, n->H, n->W, n->wchunk,
+                                                                 n->wpartial);
   k_sum_partials<<<(NOUT + 255) / 256, 256, 0, n->stream>>>(n->wpartial, n->wblocks, NOUT, grad);
 }
 
 // Loss against the target features and all gradients into n->grad.
 int loss_backward(lbm_cnn* n, const double* target) {
-  k_features<<<(n->npix + 255) / 256, 256, 0, n->stream>>>(target, n->npix, n->tf, nullptr);
+  k_features<<<(n->npix + 255) / 256, 256, 0, n->stream>>>(target, n->npix, n->tf);
   const int nel = 4 * n->npix, nb = (nel + 255) / 256;
-  k_loss<<<nb, 256, 0, n->stream>>>(n->xf, n->z, n->tf, nel, n->dz[0], n->dpart);
+  k_loss<<<nb, 256, 0, n->stream>>>(n->xf, n->z, n->tf, nel, n->dz[0], n->dpart, n->scale,
+                                    n->loss_kind == LBM_CNN_LOSS_L1);
   k_sum_d<<<1, 32, 0, n->stream>>>(n->dpart, nb, 1.0 / nel, n->dloss);
   float* g = n->grad;
   // layer 5 (32 -> 4): dz[0] holds d loss / d z5
@@ -433,7 +510,7 @@ int loss_backward(lbm_cnn* n, const double* target) {
   conv<32, 32, EPI_MASK_BF16>(n, n->dz[0], n->wb[2], nullptr, n->act[2], n->dz[1], nullptr);
   wgrad<32, 32>(n, n->act[1], n->dz[1], g + param_offset(1));
   conv<32, 32, EPI_MASK_BF16>(n, n->dz[1], n->wb[1], nullptr, n->act[1], n->dz[0], nullptr);
-  wgrad<4, 32>(n, n->act[0], n->dz[0], g + param_offset(0));
+  wgrad<4, 32>(n, (const float*)n->xf, n->dz[0], g + param_offset(0));
   CCK(n, cudaGetLastError());
   return LBM_OK;
 }
@@ -572,13 +649,54 @@ int lbm_cnn_train_step(lbm_cnn* n, const double* coarse, const double* target, d
   return LBM_OK;
 }
 
+int lbm_cnn_set_output_scale(lbm_cnn* n, const double* scale) {
+  if (!n || !scale) return cfail(n, LBM_ERR_INVALID, "NULL argument");
+  for (int c = 0; c < 4; ++c)
+    if (!(std::isfinite(scale[c]) && scale[c] > 0.0))
+      return cfail(n, LBM_ERR_INVALID, "output scales must be finite and > 0");
+  for (int c = 0; c < 4; ++c) n->scale.s[c] = (float)scale[c];
+  return LBM_OK;
+}
+
+int lbm_cnn_set_loss(lbm_cnn* n, int kind) {
+  if (!n) return cfail(nullptr, LBM_ERR_INVALID, "NULL argument");
+  if (kind != LBM_CNN_LOSS_MSE && kind != LBM_CNN_LOSS_L1)
+    return cfail(n, LBM_ERR_INVALID, "unknown loss kind");
+  n->loss_kind = kind;
+  return LBM_OK;
+}
+
+int lbm_cnn_residual_rms(lbm_cnn* n, const double* coarse, const double* target, double* rms) {
+  if (!n || !coarse || !target || !rms) return cfail(n, LBM_ERR_INVALID, "NULL argument");
+  const int nb = (n->npix + 255) / 256;
+  k_features<<<nb, 256, 0, n->stream>>>(coarse, n->npix, n->xf);
+  k_features<<<nb, 256, 0, n->stream>>>(target, n->npix, n->tf);
+  std::vector<double> part(4 * (size_t)nb);
+  double* dpart = nullptr;
+  CCK(n, cudaMalloc((void**)&dpart, sizeof(double) * part.size()));
+  k_residual_sq<<<nb, 256, 0, n->stream>>>(n->xf, n->tf, n->npix, dpart);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), dpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
+                        n->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+  cudaFree(dpart);
+  CCK(n, e);
+  for (int c = 0; c < 4; ++c) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[4 * b + c];
+    rms[c] = std::sqrt(s / n->npix);
+  }
+  return LBM_OK;
+}
+
 int lbm_cnn_correct(lbm_cnn* n, const double* coarse, double* corrected, double mass_tol,
                     int* used_fallback) {
   if (!n || !coarse || !corrected) return cfail(n, LBM_ERR_INVALID, "NULL argument");
   int rc = forward(n, coarse);
   if (rc != LBM_OK) return rc;
   const int nb = (n->npix + 255) / 256;
-  k_apply<<<nb, 256, 0, n->stream>>>(n->xf, n->z, n->npix, corrected, coarse, n->dpart);
+  k_apply<<<nb, 256, 0, n->stream>>>(n->xf, n->z, n->npix, corrected, coarse, n->dpart, n->scale);
   CCK(n, cudaGetLastError());
   std::vector<double> part(2 * (size_t)nb);
   CCK(n, cudaMemcpyAsync(part.data(), n->dpart, sizeof(double) * part.size(),

@@ -414,6 +414,9 @@ _SIGS.update({
     "lbm_cnn_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "lbm_cnn_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "lbm_cnn_correct": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_cnn_set_output_scale": (ctypes.c_int, [_vp, _vp]),
+    "lbm_cnn_set_loss": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "lbm_cnn_residual_rms": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lbm_restrict": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "lbm_cnn_last_error": (ctypes.c_char_p, [_vp]),
 })
@@ -469,6 +472,24 @@ def lbm_cnn_train_step(n, coarse, target, want_loss=True):
     _ccheck(load().lbm_cnn_train_step(n, _dev(coarse), _dev(target),
                                       ctypes.byref(loss) if want_loss else None), n)
     return loss.value if want_loss else None
+
+
+CNN_LOSS = {"mse": 0, "l1": 1}
+
+
+def lbm_cnn_set_loss(n, kind):
+    _ccheck(load().lbm_cnn_set_loss(n, CNN_LOSS[kind]), n)
+
+
+def lbm_cnn_set_output_scale(n, scale):
+    buf = (ctypes.c_double * 4)(*[float(x) for x in scale])
+    _ccheck(load().lbm_cnn_set_output_scale(n, ctypes.cast(buf, _vp)), n)
+
+
+def lbm_cnn_residual_rms(n, coarse, target):
+    buf = (ctypes.c_double * 4)()
+    _ccheck(load().lbm_cnn_residual_rms(n, _dev(coarse), _dev(target), ctypes.cast(buf, _vp)), n)
+    return list(buf)
 
 
 def lbm_cnn_correct(n, coarse, out, mass_tol=1e-2):

@@ -1,9 +1,10 @@
 """GPU tests of the learned coarse-grid corrector (include/lbm_cnn.h).
 
-* Loss and every parameter gradient of the GPU network (BF16 tensor-core
-  convolutions, FP32 accumulation) against the FP64 CPU reference
-  (oracle/cnn.py) run with the same BF16 rounding of the parameters, the
-  input features, the stored activations and the stored output gradients:
+* Loss and every parameter gradient of the GPU network (an FP32 first layer
+  on the FP32 features, then BF16 tensor-core convolutions with FP32
+  accumulation) against the FP64 CPU reference (oracle/cnn.py) run with the
+  same BF16 rounding of the later layers' parameters, the stored activations
+  and the stored output gradients:
   what is left is FP32-vs-FP64 accumulation order, so the bar is a relative
   L2 error of 2e-3 per gradient. Against the unrounded FP64 network the loss
   agrees within 1e-2 (BF16 keeps 8 significant bits; the rounded output
@@ -44,7 +45,8 @@ def _fields(rng, H, W):
     return np.stack([rho, u, v, T])
 
 
-def test_gradients_match_cpu_reference():
+@pytest.mark.parametrize("loss_kind", ["mse", "l1"])
+def test_gradients_match_cpu_reference(loss_kind):
     import torch
     from paper_0908_3749_gb300 import lbm, corrector
     rng = np.random.default_rng(0)
@@ -53,19 +55,28 @@ def test_gradients_match_cpu_reference():
     last = _unpack(params)[-1][0]
     last[...] = rng.standard_normal(last.shape) * 0.05      # non-zero last layer
     coarse, target = _fields(rng, H, W), _fields(rng, H, W)
+    scale = (0.5, 2.0, 1.0, 0.25)
     net = lbm.lbm_cnn_create(H, W)
     try:
         lbm.lbm_cnn_set_params(net, params)
+        lbm.lbm_cnn_set_output_scale(net, scale)
+        lbm.lbm_cnn_set_loss(net, loss_kind)
         loss, g = lbm.lbm_cnn_loss_grad(net, torch.tensor(coarse, device="cuda"),
                                         torch.tensor(target, device="cuda"))
+        rms = lbm.lbm_cnn_residual_rms(net, torch.tensor(coarse, device="cuda"),
+                                       torch.tensor(target, device="cuda"))
     finally:
         lbm.lbm_cnn_destroy(net)
-    ref_params = [(_bf16(w), b.astype(np.float64)) for w, b in _unpack(params)]
+    # first layer: FP32 features and FP32 weights; later layers: BF16 weights
+    ref_params = [(w.astype(np.float64) if l == 0 else _bf16(w), b.astype(np.float64))
+                  for l, (w, b) in enumerate(_unpack(params))]
     xf = cnn.features(*coarse).astype(np.float32).astype(np.float64)
-    x = _bf16(xf)
+    x = xf
     t = cnn.features(*target).astype(np.float32).astype(np.float64)
-    exact_loss, _ = cnn.loss_and_grads(x, t, ref_params, x_res=xf)
-    rloss, rgrads = cnn.loss_and_grads(x, t, ref_params, x_res=xf, store=cnn.bf16)
+    exact_loss, _ = cnn.loss_and_grads(x, t, ref_params, x_res=xf, scale=scale, loss=loss_kind)
+    rloss, rgrads = cnn.loss_and_grads(x, t, ref_params, x_res=xf, store=cnn.bf16, scale=scale,
+                                       loss=loss_kind)
+    np.testing.assert_allclose(rms, np.sqrt(((t - xf) ** 2).mean(axis=(0, 1))), rtol=1e-12)
     assert abs(loss - exact_loss) <= 1e-2 * exact_loss, (loss, exact_loss)
     assert abs(loss - rloss) <= 1e-5 * rloss, (loss, rloss)
     errs = []

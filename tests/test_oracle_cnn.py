@@ -30,13 +30,20 @@ def test_conv_matches_scipy_correlate():
         np.testing.assert_allclose(y[:, :, o], ref, rtol=1e-12, atol=1e-12)
 
 
-def test_gradients_match_finite_differences():
+@pytest.mark.parametrize("loss_kind,scale", [("mse", None), ("l1", None), ("mse", (0.5, 2.0, 1.0, 0.25)),
+                                              ("l1", (0.5, 2.0, 1.0, 0.25))])
+def test_gradients_match_finite_differences(loss_kind, scale):
+    """Backward pass of the squared and absolute losses, with and without a
+    per-channel output scale, against central differences (the absolute
+    loss is differentiable away from out = target, which random data avoid
+    at this step size)."""
     rng = np.random.default_rng(1)
     chans = [4, 5, 5, 4]
     params = _params(rng, chans)
     x = rng.standard_normal((6, 5, 4))
     t = rng.standard_normal((6, 5, 4))
-    loss, grads = cnn.loss_and_grads(x, t, params)
+    kw = dict(scale=scale, loss=loss_kind)
+    loss, grads = cnn.loss_and_grads(x, t, params, **kw)
     h = 1e-6
     for l, (w, b) in enumerate(params):
         for arr, g in ((w, grads[l][0]), (b, grads[l][1])):
@@ -45,9 +52,9 @@ def test_gradients_match_finite_differences():
             for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
                 old = flat[idx]
                 flat[idx] = old + h
-                lp, _ = cnn.loss_and_grads(x, t, params)
+                lp, _ = cnn.loss_and_grads(x, t, params, **kw)
                 flat[idx] = old - h
-                lm, _ = cnn.loss_and_grads(x, t, params)
+                lm, _ = cnn.loss_and_grads(x, t, params, **kw)
                 flat[idx] = old
                 fd = (lp - lm) / (2 * h)
                 assert abs(fd - gflat[idx]) <= 1e-6 * max(1.0, abs(fd)), (l, idx, fd, gflat[idx])
