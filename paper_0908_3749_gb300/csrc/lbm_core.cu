@@ -545,6 +545,7 @@ struct lbm_ctx {
   DevStatus* st = nullptr;
   double* partial = nullptr;
   double* staging = nullptr;
+  void* pstage = nullptr;  // contiguous populations for host transfers (on first use)
   int nblocks = 0;      // blocks of one step launch
   int ntiles = 0, tiles_x = 0;  // node tiles of the grid
   int sms = 0;          // multiprocessors of the device
@@ -700,17 +701,56 @@ int encode_tile_map(lbm_ctx* c, int b) {
   return LBM_OK;
 }
 
+// Resets the status block for time level `step` in slot `cur` (a kernel, so
+// that a restart needs no host round trip).
+__global__ void k_reset_status(DevStatus* st, int cur, unsigned long long step, int phase) {
+  constexpr int WORDS = (int)(offsetof(DevStatus, audit_totals) / sizeof(unsigned long long));
+  static_assert(offsetof(DevStatus, audit_totals) % sizeof(unsigned long long) == 0, "prefix");
+  unsigned long long* w = reinterpret_cast<unsigned long long*>(st);
+  for (int i = threadIdx.x; i < WORDS; i += blockDim.x) w[i] = 0ull;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->step[cur] = step;
+    st->audit_phase[cur] = phase;
+    st->first_bad = NONE;
+    st->first_negT = NONE;
+  }
+}
+
 int reset_status(lbm_ctx* c, unsigned long long step) {
-  DevStatus h;
-  memset(&h, 0, offsetof(DevStatus, audit_totals));
-  h.step[c->cur] = step;
-  h.audit_phase[c->cur] =
+  const int phase =
       c->cfg.audit_every > 0 ? (int)(step % (unsigned long long)c->cfg.audit_every) : 0;
-  h.first_bad = NONE;
-  h.first_negT = NONE;
-  CK(c, cudaMemcpyAsync(c->st, &h, offsetof(DevStatus, audit_totals),
-                        cudaMemcpyHostToDevice, c->stream));
-  CK(c, cudaStreamSynchronize(c->stream));
+  k_reset_status<<<1, 64, 0, c->stream>>>(c->st, c->cur, step, phase);
+  CK(c, cudaGetLastError());
+  return LBM_OK;
+}
+
+// Copies `rows` rows of nx elements between row pitches sp and dp (elements).
+template <typename T>
+__global__ void k_repitch(const T* __restrict__ src, long long sp, T* __restrict__ dst,
+                          long long dp, int nx, long long rows) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  for (long long r = blockIdx.y; r < rows; r += gridDim.y) dst[r * dp + x] = src[r * sp + x];
+}
+
+int repitch(lbm_ctx* c, const void* src, long long sp, void* dst, long long dp) {
+  const long long rows = 16ll * c->cfg.ny;
+  const dim3 grid((c->cfg.nx + 255) / 256, (unsigned)std::min(rows, 65535ll));
+  if (c->esize == 8)
+    k_repitch<double><<<grid, 256, 0, c->stream>>>((const double*)src, sp, (double*)dst, dp,
+                                                   c->cfg.nx, rows);
+  else
+    k_repitch<float><<<grid, 256, 0, c->stream>>>((const float*)src, sp, (float*)dst, dp,
+                                                  c->cfg.nx, rows);
+  CK(c, cudaGetLastError());
+  return LBM_OK;
+}
+
+// Device buffer for one contiguous copy of the populations (host transfers).
+int population_stage(lbm_ctx* c) {
+  if (!c->pstage)
+    CK(c, cudaMalloc(&c->pstage, (size_t)16 * c->cfg.nx * c->cfg.ny * c->esize));
   return LBM_OK;
 }
 
@@ -882,7 +922,9 @@ int lbm_set_init(lbm_ctx* c, const double* rho, const double* u, const double* v
     k_init<float><<<c->aux_grid, blk, 0, c->stream>>>((float*)c->f[0], p[0], p[1], p[2], p[3],
                                                    c->Kd, c->cfg.nx, c->cfg.ny, c->pitch, c->plane);
   CK(c, cudaGetLastError());
-  return reset_status(c, 0);
+  const int rc = reset_status(c, 0);
+  if (rc == LBM_OK && !on_device) CK(c, cudaStreamSynchronize(c->stream));  // host fields free again
+  return rc;
 }
 
 int lbm_step(lbm_ctx* c, long long nsteps) {
@@ -939,6 +981,7 @@ int lbm_destroy(lbm_ctx* c) {
   if (c->st) cudaFree(c->st);
   if (c->partial) cudaFree(c->partial);
   if (c->staging) cudaFree(c->staging);
+  if (c->pstage) cudaFree(c->pstage);
   if (c->tc_b) cudaFree(c->tc_b);
   if (c->tc_w) cudaFree(c->tc_w);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1017,10 +1060,18 @@ long long lbm_step_count(lbm_ctx* c) {
 int lbm_get_populations(lbm_ctx* c, void* f, long long* step, int on_device) {
   if (!c || !f) return fail(c, LBM_ERR_INVALID, "NULL argument");
   const size_t w = (size_t)c->cfg.nx * c->esize;
-  CK(c, cudaMemcpy2DAsync(f, w, c->f[c->cur], (size_t)c->pitch * c->esize, w,
-                          (size_t)16 * c->cfg.ny,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                          c->stream));
+  const size_t bytes = w * 16 * c->cfg.ny;
+  if (on_device) {
+    CK(c, cudaMemcpy2DAsync(f, w, c->f[c->cur], (size_t)c->pitch * c->esize, w,
+                            (size_t)16 * c->cfg.ny, cudaMemcpyDeviceToDevice, c->stream));
+  } else if (c->pitch == c->cfg.nx) {  // rows unpadded: one contiguous copy
+    CK(c, cudaMemcpyAsync(f, c->f[c->cur], bytes, cudaMemcpyDeviceToHost, c->stream));
+  } else {  // gather into a contiguous stage, then one copy (not 16 ny short rows)
+    int rc = population_stage(c);
+    if (rc == LBM_OK) rc = repitch(c, c->f[c->cur], c->pitch, c->pstage, c->cfg.nx);
+    if (rc != LBM_OK) return rc;
+    CK(c, cudaMemcpyAsync(f, c->pstage, bytes, cudaMemcpyDeviceToHost, c->stream));
+  }
   if (step) {
     unsigned long long s = 0;
     CK(c, cudaMemcpyAsync(&s, &c->st->step[c->cur], sizeof(s), cudaMemcpyDeviceToHost, c->stream));
@@ -1035,12 +1086,22 @@ int lbm_get_populations(lbm_ctx* c, void* f, long long* step, int on_device) {
 int lbm_set_populations(lbm_ctx* c, const void* f, long long step, int on_device) {
   if (!c || !f || step < 0) return fail(c, LBM_ERR_INVALID, "bad argument");
   const size_t w = (size_t)c->cfg.nx * c->esize;
+  const size_t bytes = w * 16 * c->cfg.ny;
   c->cur = 0;
-  CK(c, cudaMemcpy2DAsync(c->f[0], (size_t)c->pitch * c->esize, f, w, w,
-                          (size_t)16 * c->cfg.ny,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          c->stream));
-  return reset_status(c, (unsigned long long)step);
+  if (on_device) {
+    CK(c, cudaMemcpy2DAsync(c->f[0], (size_t)c->pitch * c->esize, f, w, w,
+                            (size_t)16 * c->cfg.ny, cudaMemcpyDeviceToDevice, c->stream));
+  } else if (c->pitch == c->cfg.nx) {
+    CK(c, cudaMemcpyAsync(c->f[0], f, bytes, cudaMemcpyHostToDevice, c->stream));
+  } else {  // one contiguous copy into a stage, then spread to the row pitch
+    int rc = population_stage(c);
+    if (rc != LBM_OK) return rc;
+    CK(c, cudaMemcpyAsync(c->pstage, f, bytes, cudaMemcpyHostToDevice, c->stream));
+    if ((rc = repitch(c, c->pstage, c->cfg.nx, c->f[0], c->pitch)) != LBM_OK) return rc;
+  }
+  const int rc = reset_status(c, (unsigned long long)step);
+  if (rc == LBM_OK && !on_device) CK(c, cudaStreamSynchronize(c->stream));  // host f is free again
+  return rc;
 }
 
 int lbm_element_size(lbm_ctx* c) { return c ? c->esize : 0; }
