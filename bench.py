@@ -184,6 +184,24 @@ def device_uuid(torch):
         return None
 
 
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum of ``values`` (floats) over all ranks of the
+    process group (``dist`` None: one process, the values themselves). The
+    slowest rank's time is the job's time."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units processed by all ranks (each rank the same work: weak scaling,
+    independent replicas) per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def time_steps(torch, lbm, ctx, stream, flush, K, W):
     """Per-step CUDA-event times (ms) of K steps after W warm-up steps."""
     with torch.cuda.stream(stream):
@@ -402,12 +420,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     blocks32, blocks64 = lbm.lbm_step_blocks(ctx32), lbm.lbm_step_blocks(ctx64)
-    total32 = sum(t32)
-    total64 = sum(t64)
-    if dist:
-        t = torch.tensor([total32, total64], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total32, total64 = t.tolist()
+    total32, total64 = max_over_ranks(dist, [sum(t32), sum(t64)], "cuda")
 
     # accuracy of the FP32 path against the FP64 path after the same steps
     m32 = [np.empty((w.ny, w.nx)) for _ in range(4)]
@@ -467,7 +480,7 @@ def run_ours(args):
     tflops64 = FLOPS_PER_CELL * cells / (ms64 * 1e-3) / 1e12
     line = {
         "metric": METRIC,
-        "value": world * cells * K / (total32 * 1e-3),
+        "value": whole_job_rate(world, cells * K, total32 * 1e-3),
         "unit": UNIT,
         "n_gpus": world,
         "steps": K,
@@ -485,7 +498,7 @@ def run_ours(args):
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                      "bytes_per_cell_update": BYTES_PER_CELL["fp32"]},
         "accuracy_fp32_vs_fp64": acc,
-        "fp64": {"value": world * cells * K / (total64 * 1e-3), "unit": UNIT,
+        "fp64": {"value": whole_job_rate(world, cells * K, total64 * 1e-3), "unit": UNIT,
                  "ms_per_step": ms64, "dtype": "f64", "step_blocks": blocks64,
                  "roofline": {"bound": "alu", "achieved": tflops64, "peak": FP64_PEAK_TFLOPS,
                               "unit": "TFLOP/s", "frac": tflops64 / FP64_PEAK_TFLOPS,
