@@ -117,6 +117,43 @@ def sod_paper_case1():
 
 
 # ----------------------------------------------------------------------------
+# The paper's other shock tubes (Sec. V.A(b)-(e)) and the single-relaxation
+# version (Sec. II: S = I / tau; the paper's tau = 1e-5 gives every s = 1e5)
+# ----------------------------------------------------------------------------
+# name: (left, right, t_end, {case: (dx, dt)}, MRT rates, domain [a, b]); the
+# domain (not stated in the paper) holds every wave of the gamma = 2 exact
+# solution at t_end with a margin.
+PAPER_TUBES = {
+    "lax": ((0.445, 0.698, 0.0, 7.928), (0.5, 0.0, 0.0, 1.142), 0.2,
+            {1: (0.004, 4e-6), 2: (0.002, 2e-6), 3: (0.001, 1e-6)},
+            rates(s7=3e3, s8=3e3, s13=1e2), (-0.8, 0.8)),
+    "colella": ((1.0, 0.0, 0.0, 1000.0), (1.0, 0.0, 0.0, 0.01), 0.1,
+                {1: (0.002, 2e-6), 2: (0.001, 1e-6)},
+                rates(s7=5e4, s8=5e4, s11=5e5, s13=5e5), (-5.0, 3.0)),
+    "two_shock": ((5.99924, 19.5975, 0.0, 76.8254), (5.99242, -6.19633, 0.0, 7.69222), 0.1,
+                  {1: (0.003, 1e-5)}, rates(s5=5e3, s6=5e3, s7=3e4, s8=3e4), (-0.5, 1.8)),
+    "high_mach": ((5.0, 45.0, 0.0, 10.0), (6.0, -20.0, 0.0, 5.0), 0.018,
+                  {1: (0.003, 1e-5)}, rates(s5=1.5e4, s6=1.5e4, s10=5e4), (-0.3, 0.7)),
+}
+SRT_RATES = rates()   # every s = 1 / tau = 1e5
+
+
+def paper_tube(name, case=1, srt=False, ny=1):
+    """Sec. V.A shock tube ``name`` (lax, colella, two_shock, high_mach) at
+    the paper's grid and time step of ``case``, the paper's MRT rates or
+    (srt) the single relaxation time tau = 1e-5, on x in [a, b] with the
+    interface at x = 0; nsteps reaches the paper's t_end. meta holds a, the
+    end time and the two states (for the exact solution)."""
+    left, right, t_end, grids, mrt, (a, b) = PAPER_TUBES[name]
+    dx, dt = grids[case]
+    nx = int(round((b - a) / dx))
+    w = shock_tube(left, right, nx, dx, dt, int(round(t_end / dt)), SRT_RATES if srt else mrt,
+                   ny=ny, x_interface=-a, name="%s_case%d_%s" % (name, case, "srt" if srt else "mrt"))
+    w.meta.update(a=a, t_end=t_end)
+    return w
+
+
+# ----------------------------------------------------------------------------
 # Regular shock reflection (Sec. V.B.a geometry)
 # ----------------------------------------------------------------------------
 # Paper's Mach-5 problem: inflow (1, 5, 0, 0.5), top (2.27273, 4.3, -1.21244, 1.76).
