@@ -349,14 +349,7 @@ def tubes_measure(torch, lbm, stream, args):
     nt = len(B["nx"])
     b = lbm.lbm_batch_create(B["nx"], B["dx"], B["dt"], B["s"], B["left"], B["right"], stream)
     try:
-        fields = []
-        for q in range(4):
-            parts = []
-            for t in range(nt):
-                x = (np.arange(B["nx"][t]) + 0.5) / B["nx"][t]
-                parts.append(np.where(x <= 0.5, B["left"][t, q], B["right"][t, q]))
-            fields.append(np.concatenate(parts))
-        lbm.lbm_batch_set_init(b, *fields)
+        lbm.lbm_batch_set_init(b, *workloads.tube_fields(B))
         chosen = lbm.lbm_batch_autotune(b, 20, None)
         n = args.tube_steps
         lbm.lbm_batch_step(b, n)               # capture + warm-up

@@ -90,6 +90,17 @@ enum lbm_bc_kind {
 typedef struct {
   int kind;              /* lbm_bc_kind */
   double rho, u, v, T;   /* used by LBM_BC_EQ (all four) and LBM_BC_WALL (u, v, T) */
+  /* Optional split of the side (0: the whole side is `kind`). With split = 1
+   * a ghost node at position s along the side (its cell-centred x on the y
+   * sides, y on the x sides) takes `kind` where s <= split0 + split_rate * t
+   * and `far_kind` beyond, t = time level x dt of the state being advanced:
+   * e.g. the Mach reflection of Sec. V.B.b, whose bottom is the post-shock
+   * inflow up to x = 150 dx and reflecting beyond, and whose top switches
+   * from inflow to extrapolation at x = g(t) moving with the incident shock.
+   * Neither kind may be LBM_BC_PERIODIC; both share the state above. */
+  int split;
+  int far_kind;          /* lbm_bc_kind beyond the split */
+  double split0, split_rate;
 } lbm_bc;
 
 typedef struct {

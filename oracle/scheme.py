@@ -38,6 +38,10 @@ R7  Extrapolating side: ghost q = 2 q_1 - q_2 for q in (rho, u, v, T), q_1 the
 R8  Moving isothermal wall (Couette, Sec. V.D: "constant speed and constant
     temperature"): the ghost state is (rho of the adjacent node, u_w, v_w,
     T_w); the paper does not say what density the wall node carries.
+R22 Side split along its length (Mach reflection, Sec. V.B.b): the ghost
+    of the node at s = (index + 1/2) h along the side takes the near kind
+    where s <= s0 + s1 t and the far kind beyond, t the time of the state
+    being advanced (the paper's g(t) for the top, 150 dx for the bottom).
 R20 Open side of problems the paper does not pose (2D Riemann quadrants):
     zero-gradient outflow, the ghost state is the adjacent node's state
     (zero-order extrapolation; the first-order one of R7 amplifies waves that
@@ -141,9 +145,19 @@ def _extrapolate(q1, q2):
     return [np.where(bad, a, b) for a, b in zip(q1, qe)]
 
 
-def _ghost_line(f, side, bc):
+def _ghost_line(f, side, bc, t=0.0, h=1.0):
     """Ghost populations next to one side, shape (16, n) (n = ny for x sides,
-    nx for y sides), from the interior f (16, ny, nx) at time n."""
+    nx for y sides), from the interior f (16, ny, nx) at time t. ``bc`` is
+    (kind, state) or, for a side split along its length (reading R22),
+    (kind, state, (far_kind, s0, s1)): the ghost of the node at position
+    s = (index + 1/2) h along the side takes ``kind`` where s <= s0 + s1 t
+    and ``far_kind`` beyond."""
+    if len(bc) > 2 and bc[2] is not None:
+        far, s0, s1 = bc[2]
+        near_line = _ghost_line(f, side, bc[:2])
+        far_line = _ghost_line(f, side, (far, bc[1]))
+        s = (np.arange(near_line.shape[1]) + 0.5) * h
+        return np.where(s <= s0 + s1 * t, near_line, far_line)
     kind, state = bc
     xs = side[0] == "x"
     lo = side[1] == "-"
@@ -184,17 +198,17 @@ def _ghost_line(f, side, bc):
     raise ValueError("unknown boundary kind %r" % (kind,))
 
 
-def padded(f, bcs):
-    """Interior f (16, ny, nx) surrounded by one ring of ghost nodes
-    (16, ny+2, nx+2). Corner ghosts are NaN: the cross stencil never reads
-    them (reading R5)."""
+def padded(f, bcs, t=0.0, dx=1.0, dy=1.0):
+    """Interior f (16, ny, nx) at time t surrounded by one ring of ghost
+    nodes (16, ny+2, nx+2). Corner ghosts are NaN: the cross stencil never
+    reads them (reading R5)."""
     q, ny, nx = f.shape
     g = np.full((q, ny + 2, nx + 2), np.nan)
     g[:, 1:-1, 1:-1] = f
-    g[:, 1:-1, 0] = _ghost_line(f, "x-", bcs[0])
-    g[:, 1:-1, -1] = _ghost_line(f, "x+", bcs[1])
-    g[:, 0, 1:-1] = _ghost_line(f, "y-", bcs[2])
-    g[:, -1, 1:-1] = _ghost_line(f, "y+", bcs[3])
+    g[:, 1:-1, 0] = _ghost_line(f, "x-", bcs[0], t, dy)
+    g[:, 1:-1, -1] = _ghost_line(f, "x+", bcs[1], t, dy)
+    g[:, 0, 1:-1] = _ghost_line(f, "y-", bcs[2], t, dx)
+    g[:, -1, 1:-1] = _ghost_line(f, "y+", bcs[3], t, dx)
     return g
 
 
@@ -224,13 +238,13 @@ def advection(g, dx, dy, dt):
             - vy * vy * dt * (n_ - 2.0 * c + s_) / (2.0 * dy * dy))
 
 
-def step(f, cfg):
-    """One time step of Eq. 3 discretised by Eq. A.1:
+def step(f, cfg, t=0.0):
+    """One time step of Eq. 3 discretised by Eq. A.1 from time t:
     f(t+dt) = f - dt * [v.grad f]_A.1b + Delta f_collision, all terms at t.
 
-    ``cfg`` needs keys dx, dy, dt, s (16 rates) and bc (4 pairs (kind, state)
-    for sides x-, x+, y-, y+)."""
-    g = padded(f, cfg["bc"])
+    ``cfg`` needs keys dx, dy, dt, s (16 rates) and bc (4 pairs (kind, state),
+    or split triples, for sides x-, x+, y-, y+)."""
+    g = padded(f, cfg["bc"], t, cfg["dx"], cfg["dy"])
     dt = cfg["dt"]
     return f - dt * advection(g, cfg["dx"], cfg["dy"], dt) + collision(f, cfg["s"], dt)
 
@@ -241,16 +255,17 @@ def init_populations(rho, u, v, T):
     return equilibrium_populations(rho, u, v, T)
 
 
-def run(f, cfg, nsteps, check_every=0):
-    """Advance ``nsteps`` steps. Returns (f, first_bad) where first_bad is the
-    first checked time level (0 = the input state) at which some node is
+def run(f, cfg, nsteps, check_every=0, level0=0):
+    """Advance ``nsteps`` steps from time level ``level0`` (time level0 dt).
+    Returns (f, first_bad) where first_bad is the first checked time level
+    (counted from level0 = the input state) at which some node is
     non-finite or has rho <= 0, checked every ``check_every`` steps
     (0: never); the run stops there."""
     check_bcs(cfg["bc"])
     for n in range(nsteps):
         if check_every and n % check_every == 0 and not physical(f):
             return f, n
-        f = step(f, cfg)
+        f = step(f, cfg, (level0 + n) * cfg["dt"])
     if check_every and not physical(f):
         return f, nsteps
     return f, None

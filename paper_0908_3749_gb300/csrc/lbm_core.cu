@@ -70,7 +70,7 @@ __device__ __forceinline__ void load_tile(R* stage, const CUtensorMap* tmap, uns
 template <typename R, typename Off>
 __device__ __forceinline__ void step_tile(const StepArgs<R>& A, const R* __restrict__ fin,
                                           R* __restrict__ fout, const R* stage, int cur, bool audit,
-                                          double (*sm)[4], bool& bad, bool& negT) {
+                                          R t, double (*sm)[4], bool& bad, bool& negT) {
   constexpr int BXD = Shape<R>::X, BYD = Shape<R>::Y, N = BXD * BYD;
   constexpr int BXP = Tile<R>::BXP, PS = Tile<R>::ROWS * BXP;
   const int x = (cur % A.tiles_x) * BXD + threadIdx.x;
@@ -95,7 +95,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<R>& A, const R* __restr
     bad |= b;
     negT |= !b && !(press > R(0));
     mc[0] = m.rho; mc[1] = m.jx; mc[2] = m.jy; mc[3] = m.e;
-    neighbour_terms<R, Off, BXP>(A, fin, ctr, PS, P, pitch, c, x, y, m, acc);
+    neighbour_terms<R, Off, BXP>(A, fin, ctr, PS, P, pitch, c, x, y, m, t, acc);
 #pragma unroll
     for (int i = 0; i < 16; ++i) fout[i * P + c] = acc[i];
   }
@@ -114,7 +114,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<R>& A, const R* __restr
 template <typename Off>
 __device__ __forceinline__ void step_tile_x2(const StepArgs<float>& A, const float* __restrict__ fin,
                                              float* __restrict__ fout, const float* stage, int cur,
-                                             bool audit, double (*sm)[4], bool& bad, bool& negT) {
+                                             bool audit, float t, double (*sm)[4], bool& bad,
+                                             bool& negT) {
   constexpr int BXD = Shape<float>::X, BYD = Shape<float>::Y, HY = BYD / 2;
   constexpr int BXP = Tile<float>::BXP, PS = Tile<float>::ROWS * BXP;
   static_assert(Shape<float>::TY == HY, "two rows per thread");
@@ -165,14 +166,14 @@ __device__ __forceinline__ void step_tile_x2(const StepArgs<float>& A, const flo
 #pragma unroll
       for (int i = 0; i < 16; ++i) acc1[i] = acc[i].v.x;
       const Cons<float> m1 = {m.rho.v.x, m.jx.v.x, m.jy.v.x, m.e.v.x};
-      neighbour_terms<float, Off, BXP>(A, fin, sa, PS, P, pitch, ca, x, ya, m1, acc1);
+      neighbour_terms<float, Off, BXP>(A, fin, sa, PS, P, pitch, ca, x, ya, m1, t, acc1);
 #pragma unroll
       for (int i = 0; i < 16; ++i) fout[i * P + ca] = acc1[i];
       if (act_b) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) acc1[i] = acc[i].v.y;
         const Cons<float> m2 = {m.rho.v.y, m.jx.v.y, m.jy.v.y, m.e.v.y};
-        neighbour_terms<float, Off, BXP>(A, fin, sb, PS, P, pitch, cb, x, yb, m2, acc1);
+        neighbour_terms<float, Off, BXP>(A, fin, sb, PS, P, pitch, cb, x, yb, m2, t, acc1);
 #pragma unroll
         for (int i = 0; i < 16; ++i) fout[i * P + cb] = acc1[i];
       }
@@ -200,11 +201,11 @@ __device__ __forceinline__ void step_tile_x2(const StepArgs<float>& A, const flo
 template <typename R, typename Off>
 __device__ __forceinline__ void step_any(const StepArgs<R>& A, const R* __restrict__ fin,
                                          R* __restrict__ fout, const R* stage, int cur, bool audit,
-                                         double (*sm)[4], bool& bad, bool& negT) {
+                                         R t, double (*sm)[4], bool& bad, bool& negT) {
   if constexpr (Shape<R>::TY == Shape<R>::Y)
-    step_tile<R, Off>(A, fin, fout, stage, cur, audit, sm, bad, negT);
+    step_tile<R, Off>(A, fin, fout, stage, cur, audit, t, sm, bad, negT);
   else
-    step_tile_x2<Off>(A, fin, fout, stage, cur, audit, sm, bad, negT);
+    step_tile_x2<Off>(A, fin, fout, stage, cur, audit, t, sm, bad, negT);
 }
 
 template <typename R, typename Off>
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB)
     return;
   }
   bool bad = false, negT = false;
-  step_any<R, Off>(A, fin, fout, tile, blockIdx.x, audit, sm, bad, negT);
+  step_any<R, Off>(A, fin, fout, tile, blockIdx.x, audit, A.dtr * R(s_step), sm, bad, negT);
   const unsigned long long step = s_step;
   watchdog_flags(A.st, step, bad, negT);
   if (audit) audit_finish<N>(A, step, sm, &s_last);
@@ -293,7 +294,8 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB_PIP
       }
       return;
     }
-    step_any<R, Off>(A, fin, fout, stages + s * Tile<R>::ELEMS, cur, s_audit != 0, sm, bad, negT);
+    step_any<R, Off>(A, fin, fout, stages + s * Tile<R>::ELEMS, cur, s_audit != 0,
+                     A.dtr * R(s_step), sm, bad, negT);
     __syncthreads();  // stage s and sm are free again
   }
   const unsigned long long step = s_step;
@@ -586,8 +588,15 @@ StepArgs<R> make_args(lbm_ctx* c, int slot) {
   A.ny = c->cfg.ny;
   A.pitch = c->pitch;
   A.plane = c->plane;
+  A.hx = (R)c->cfg.dx;
+  A.hy = (R)c->cfg.dy;
+  A.dtr = (R)c->cfg.dt;
   for (int s = 0; s < 4; ++s) {
     A.bc[s] = c->cfg.bc[s].kind;
+    A.split[s] = c->cfg.bc[s].split;
+    A.far[s] = c->cfg.bc[s].far_kind;
+    A.s0[s] = (R)c->cfg.bc[s].split0;
+    A.s1[s] = (R)c->cfg.bc[s].split_rate;
     A.wall[s][0] = (R)c->cfg.bc[s].u;
     A.wall[s][1] = (R)c->cfg.bc[s].v;
     A.wall[s][2] = (R)c->cfg.bc[s].T;
@@ -785,10 +794,17 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
     const lbm_bc& b = C.bc[s];
     if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_OUTFLOW)
       return fail(nullptr, LBM_ERR_INVALID, "bad boundary kind");
-    if (b.kind == LBM_BC_EQ && !(finite_pos(b.rho) && finite_pos(b.T) &&
-                                 std::isfinite(b.u) && std::isfinite(b.v)))
+    if (b.split != 0 && b.split != 1) return fail(nullptr, LBM_ERR_INVALID, "split must be 0 or 1");
+    if (b.split && (b.far_kind <= LBM_BC_PERIODIC || b.far_kind > LBM_BC_OUTFLOW ||
+                    b.kind == LBM_BC_PERIODIC || !std::isfinite(b.split0) ||
+                    !std::isfinite(b.split_rate)))
+      return fail(nullptr, LBM_ERR_INVALID,
+                  "a split side needs two non-periodic kinds and a finite split position");
+    const bool eq = b.kind == LBM_BC_EQ || (b.split && b.far_kind == LBM_BC_EQ);
+    const bool wall = b.kind == LBM_BC_WALL || (b.split && b.far_kind == LBM_BC_WALL);
+    if (eq && !(finite_pos(b.rho) && finite_pos(b.T) && std::isfinite(b.u) && std::isfinite(b.v)))
       return fail(nullptr, LBM_ERR_INVALID, "Dirichlet state needs rho > 0, T > 0");
-    if (b.kind == LBM_BC_WALL && !(finite_pos(b.T) && std::isfinite(b.u) && std::isfinite(b.v)))
+    if (wall && !(finite_pos(b.T) && std::isfinite(b.u) && std::isfinite(b.v)))
       return fail(nullptr, LBM_ERR_INVALID, "wall state needs T > 0");
   }
   if ((C.bc[0].kind == LBM_BC_PERIODIC) != (C.bc[1].kind == LBM_BC_PERIODIC) ||
@@ -866,7 +882,7 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
     double states[16];
     double* dstates = nullptr;
     for (int s = 0; s < 4; ++s) {
-      const bool eq = C.bc[s].kind == LBM_BC_EQ;
+      const bool eq = C.bc[s].kind == LBM_BC_EQ || (C.bc[s].split && C.bc[s].far_kind == LBM_BC_EQ);
       states[4 * s] = eq ? C.bc[s].rho : 1.0;
       states[4 * s + 1] = eq ? C.bc[s].u : 0.0;
       states[4 * s + 2] = eq ? C.bc[s].v : 0.0;

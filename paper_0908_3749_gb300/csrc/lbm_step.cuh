@@ -59,6 +59,10 @@ struct StepArgs {
   int nx, ny;
   long long pitch, plane;
   int bc[4];          // x-, x+, y-, y+
+  int split[4];       // side split into bc (s <= s0 + s1 t) and far (beyond)
+  int far[4];
+  R s0[4], s1[4];
+  R hx, hy, dtr;      // dx, dy, dt (positions along a side, time)
   R wall[4][3];       // (u, v, T) of LBM_BC_WALL sides
   const R* geq;       // [4][16] Dirichlet ghost populations
   DevStatus* st;
@@ -149,14 +153,23 @@ __device__ __forceinline__ Cons<R> load_cons(const Coeffs<R>& K, const R* __rest
   return conserved(K, d);
 }
 
-// Ghost populations outside `side` of the node with conserved moments `own`.
-// `inward` is the index of the next node inwards (EXTRAP), `has_inward`
-// false when the grid is one node deep in that direction.
+// Boundary kind of the ghost next to node `along` (its index along the side)
+// at time t: the side's kind, or its far kind beyond a split.
+template <typename R>
+__device__ __forceinline__ int side_kind(const StepArgs<R>& A, int side, int along, R t) {
+  if (!A.split[side]) return A.bc[side];
+  const R s = (R(along) + R(0.5)) * (side < 2 ? A.hy : A.hx);
+  return s <= A.s0[side] + A.s1[side] * t ? A.bc[side] : A.far[side];
+}
+
+// Ghost populations of boundary kind `kind` outside `side` of the node with
+// conserved moments `own`. `inward` is the index of the next node inwards
+// (EXTRAP), `has_inward` false when the grid is one node deep in that
+// direction.
 template <typename R, typename Off>
 __device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict__ fin,
-                                      Off plane, int side, Cons<R> own, Off inward,
+                                      Off plane, int side, int kind, Cons<R> own, Off inward,
                                       bool has_inward, R g[16]) {
-  const int kind = A.bc[side];
   if (kind == LBM_BC_EQ) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) g[i] = A.geq[side * 16 + i];
@@ -218,7 +231,8 @@ struct Tile {
 template <typename R, typename Off, int BXP>
 __device__ __forceinline__ void neighbour_terms(const StepArgs<R>& A, const R* __restrict__ fin,
                                                 const R* ctr, int PS, Off P, Off pitch, Off c,
-                                                int x, int y, const Cons<R>& m, R (&acc)[16]) {
+                                                int x, int y, const Cons<R>& m, R t,
+                                                R (&acc)[16]) {
   if (x > 0 && x < A.nx - 1 && y > 0 && y < A.ny - 1) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -247,7 +261,7 @@ __device__ __forceinline__ void neighbour_terms(const StepArgs<R>& A, const R* _
       if (has_x(i)) acc[i] += A.K.aW[i] * fin[i * P + n];
   } else {
     R g[16];
-    ghost(A, fin, P, 0, m, c + 1, A.nx > 1, g);
+    ghost(A, fin, P, 0, side_kind(A, 0, y, t), m, c + 1, A.nx > 1, g);
 #pragma unroll
     for (int i = 0; i < 16; ++i)
       if (has_x(i)) acc[i] += A.K.aW[i] * g[i];
@@ -264,7 +278,7 @@ __device__ __forceinline__ void neighbour_terms(const StepArgs<R>& A, const R* _
       if (has_x(i)) acc[i] += A.K.aE[i] * fin[i * P + n];
   } else {
     R g[16];
-    ghost(A, fin, P, 1, m, c - 1, A.nx > 1, g);
+    ghost(A, fin, P, 1, side_kind(A, 1, y, t), m, c - 1, A.nx > 1, g);
 #pragma unroll
     for (int i = 0; i < 16; ++i)
       if (has_x(i)) acc[i] += A.K.aE[i] * g[i];
@@ -281,7 +295,7 @@ __device__ __forceinline__ void neighbour_terms(const StepArgs<R>& A, const R* _
       if (has_y(i)) acc[i] += A.K.aS[i] * fin[i * P + n];
   } else {
     R g[16];
-    ghost(A, fin, P, 2, m, c + pitch, A.ny > 1, g);
+    ghost(A, fin, P, 2, side_kind(A, 2, x, t), m, c + pitch, A.ny > 1, g);
 #pragma unroll
     for (int i = 0; i < 16; ++i)
       if (has_y(i)) acc[i] += A.K.aS[i] * g[i];
@@ -298,7 +312,7 @@ __device__ __forceinline__ void neighbour_terms(const StepArgs<R>& A, const R* _
       if (has_y(i)) acc[i] += A.K.aN[i] * fin[i * P + n];
   } else {
     R g[16];
-    ghost(A, fin, P, 3, m, c - pitch, A.ny > 1, g);
+    ghost(A, fin, P, 3, side_kind(A, 3, x, t), m, c - pitch, A.ny > 1, g);
 #pragma unroll
     for (int i = 0; i < 16; ++i)
       if (has_y(i)) acc[i] += A.K.aN[i] * g[i];

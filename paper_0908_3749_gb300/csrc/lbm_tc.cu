@@ -272,7 +272,8 @@ __global__ void __launch_bounds__(TC_N, 1)
     bad = !(c.rho > 0.f) || ((__float_as_uint(c.rho + c.jx + c.jy + c.e) & 0x7f800000u) == 0x7f800000u);
     negT = !bad && !(press > 0.f);
     cons[0] = c.rho; cons[1] = c.jx; cons[2] = c.jy; cons[3] = c.e;
-    neighbour_terms<float, unsigned, TC_BXP>(A, fin, ctr, PS, P, pitch, cidx, x, y, c, acc);
+    neighbour_terms<float, unsigned, TC_BXP>(A, fin, ctr, PS, P, pitch, cidx, x, y, c,
+                                             A.dtr * (float)step, acc);
 #pragma unroll
     for (int i = 0; i < 16; ++i) fout[i * P + cidx] = acc[i];
   }

@@ -38,7 +38,9 @@ class LBMError(RuntimeError):
 
 class lbm_bc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("rho", ctypes.c_double), ("u", ctypes.c_double),
-                ("v", ctypes.c_double), ("T", ctypes.c_double)]
+                ("v", ctypes.c_double), ("T", ctypes.c_double), ("split", ctypes.c_int),
+                ("far_kind", ctypes.c_int), ("split0", ctypes.c_double),
+                ("split_rate", ctypes.c_double)]
 
 
 class lbm_config(ctypes.Structure):
@@ -128,7 +130,10 @@ def _dev(t):
 def make_config(nx, ny, dx, dy, dt, s, bc, precision="fp64", audit_every=0,
                 internal_dof=0):
     """lbm_config from plain values; ``bc`` is four (kind, state) pairs for
-    x-, x+, y-, y+ with kind a name in ``BC`` and state (rho, u, v, T) or None."""
+    x-, x+, y-, y+ with kind a name in ``BC`` and state (rho, u, v, T) or
+    None, or (kind, state, (far_kind, split0, split_rate)) for a split side:
+    ``kind`` where the position along the side is <= split0 + split_rate t,
+    ``far_kind`` beyond."""
     c = lbm_config()
     c.nx, c.ny = int(nx), int(ny)
     c.dx, c.dy, c.dt = float(dx), float(dy), float(dt)
@@ -136,10 +141,16 @@ def make_config(nx, ny, dx, dy, dt, s, bc, precision="fp64", audit_every=0,
         c.s[k] = float(s[k])
     c.internal_dof = int(internal_dof)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    for k, (kind, state) in enumerate(bc):
+    for k, side in enumerate(bc):
+        kind, state = side[0], side[1]
         c.bc[k].kind = BC[kind] if isinstance(kind, str) else int(kind)
         if state is not None:
             c.bc[k].rho, c.bc[k].u, c.bc[k].v, c.bc[k].T = (float(x) for x in state)
+        if len(side) > 2 and side[2] is not None:
+            far, s0, s1 = side[2]
+            c.bc[k].split = 1
+            c.bc[k].far_kind = BC[far] if isinstance(far, str) else int(far)
+            c.bc[k].split0, c.bc[k].split_rate = float(s0), float(s1)
     c.audit_every = int(audit_every)
     return c
 

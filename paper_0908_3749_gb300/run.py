@@ -1,6 +1,7 @@
 """Command-line runner: one of the synthetic workloads stepped through the C ABI.
 
     python -m paper_0908_3749_gb300.run --workload reflection --precision fp32 --steps 100
+    python -m paper_0908_3749_gb300.run --workload tubes --steps 20 --autotune 5
 
 Prints one JSON line with the step count, the watchdog status, the
 conservation totals and the ranges of rho, u, v, T. Nothing is timed; it is
@@ -15,7 +16,8 @@ import numpy as np
 
 from . import lbm
 
-WORKLOADS = ("reflection", "bubble", "sod", "couette", "random")
+WORKLOADS = ("reflection", "bubble", "sod", "couette", "random", "mach", "heavy_bubble",
+             "tubes")
 
 
 def make_workload(name, nx=None, ny=None):
@@ -28,6 +30,10 @@ def make_workload(name, nx=None, ny=None):
         return W.sod_config1()
     if name == "couette":
         return W.couette()
+    if name == "mach":
+        return W.mach_reflection()
+    if name == "heavy_bubble":
+        return W.heavy_bubble(nx=nx or 2048, ny=ny or 1024)
     return W.random_state(nx or 256, ny or 128, seed=0)
 
 
@@ -44,6 +50,8 @@ def main(argv=None):
     ap.add_argument("--autotune", type=int, default=0,
                     help="if > 0, choose the launch shape with lbm_autotune(launches)")
     args = ap.parse_args(argv)
+    if args.workload == "tubes":
+        return run_tubes(args)
 
     w = make_workload(args.workload, args.nx, args.ny)
     cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, args.precision,
@@ -69,6 +77,28 @@ def main(argv=None):
         lbm.lbm_destroy(ctx)
     print(json.dumps(out))
     return 0 if rc == lbm.LBM_OK else 1
+
+
+def run_tubes(args):
+    """The seeded tube batch (``--nx`` tubes, default 4096) in one persistent
+    launch per ``lbm_batch_step`` call of ``--steps`` steps."""
+    import workloads as W
+    B = W.tube_batch(ntubes=args.nx or 4096)
+    nt = len(B["nx"])
+    b = lbm.lbm_batch_create(B["nx"], B["dx"], B["dt"], B["s"], B["left"], B["right"])
+    try:
+        lbm.lbm_batch_set_init(b, *W.tube_fields(B))
+        if args.autotune > 0:
+            lbm.lbm_batch_autotune(b, args.autotune, None)
+        lbm.lbm_batch_step(b, args.steps)
+        rc, bad, nbad, to = lbm.lbm_batch_status(b, nt)
+        out = {"workload": "tubes", "tubes": nt, "nodes": lbm.lbm_batch_total_nodes(b),
+               "steps": lbm.lbm_batch_step_count(b), "tiling": list(lbm.lbm_batch_get_tiling(b)),
+               "status": rc, "unstable_tubes": nbad, "timeout": to}
+    finally:
+        lbm.lbm_batch_destroy(b)
+    print(json.dumps(out))
+    return 0 if rc == lbm.LBM_OK and to == 0 else 1
 
 
 if __name__ == "__main__":

@@ -37,6 +37,9 @@ def test_library_exports_every_declared_symbol():
     ({"internal_dof": 3}, -2), ({"precision": 7}, -2),
     ({"s0": float("nan")}, -1), ({"bc0": ("periodic", None)}, -1),   # periodic on one side only
     ({"audit_every": -1}, -1),
+    ({"bc0": ("eq", (1, 0, 0, 1), ("periodic", 0.0, 0.0))}, -1),      # split into periodic
+    ({"bc0": ("extrap", None, ("eq", 0.0, 0.0))}, -1),               # far Dirichlet state missing
+    ({"bc0": ("eq", (1, 0, 0, 1), ("reflect", float("inf"), 0.0))}, -1),
 ])
 def test_create_rejects_bad_configs_on_host(change, code):
     from paper_0908_3749_gb300 import lbm

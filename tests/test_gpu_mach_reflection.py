@@ -1,0 +1,70 @@
+"""GPU runs with split sides (reading R22): the Mach reflection of
+Sec. V.B.b at the paper's size (600 x 300, dx = 0.003, dt = 1e-5) -- FP64
+parity with the oracle over the first 40 steps (the top side's split moves
+every step), and the run to the paper's t = 0.25 in FP64, which must stay
+physical with the incident shock on the top row within 2 nodes of g(t) --
+and the heavy bubble of Sec. V.C (parity on a small grid; the run to the
+paper's t = 0.9 with the incident shock at its Rankine-Hugoniot position)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from harness import field_errors, fp64_tol, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+def test_mach_reflection_fp64_parity_full_size():
+    w = W.mach_reflection()
+    n = 40
+    got, _, status = gpu_run(w, n, "fp64")
+    ref, _ = oracle_run(w, n)
+    err = field_errors(got, ref)
+    assert max(err.values()) <= fp64_tol(n), err
+
+
+def test_mach_reflection_to_t025_shock_follows_top_split():
+    w = W.mach_reflection()
+    got, _, status = gpu_run(w, w.nsteps, "fp64")
+    assert status[0] == 0 and status[1] == -1
+    t = w.nsteps * w.dt
+    g = w.meta["foot"] + math.tan(math.pi / 6) * (w.meta["H"] + 1.5 * t / math.sin(math.pi / 6))
+    rho = got["rho"][-2]
+    mid = 0.5 * (W.MACH_PRE[0] + W.MACH_POST[0])
+    i = int(np.where(rho < mid)[0][0])
+    x = (i - 0.5) * w.dx + (rho[i - 1] - mid) / (rho[i - 1] - rho[i]) * w.dx
+    print("Mach reflection t = %.3f: incident shock on the top row at x = %.4f, g(t) = %.4f" % (t, x, g))
+    assert abs(x - g) < 2 * w.dx
+
+
+def test_heavy_bubble_small_parity():
+    w = W.heavy_bubble(nx=192, ny=96, radius=24)
+    got, _, _ = gpu_run(w, 60, "fp64")
+    ref, _ = oracle_run(w, 60)
+    assert max(field_errors(got, ref).values()) <= fp64_tol(60)
+
+
+def test_heavy_bubble_to_paper_time_shock_speed():
+    """The heavy bubble at the paper's dx = 0.003, dt = 1e-5 to t = 0.9
+    (90 000 steps, FP32) on 1024 x 512 nodes: the run stays physical, and on
+    the wall rows (128 nodes clear of the bubble) the incident shock has
+    moved at its Rankine-Hugoniot speed s = rho2 u2 / (rho2 - rho1) (the
+    gas ahead is at rest) to within 3 nodes."""
+    w = W.heavy_bubble(nx=1024, ny=512, dx=0.003, radius=128, nsteps=90000)
+    got, _, status = gpu_run(w, w.nsteps, "fp32")
+    assert status[0] == 0 and status[1] == -1
+    assert (got["rho"] > 0).all() and (got["T"] > 0).all()
+    rho1, rho2, u2 = W.BUBBLE_PRE[0], W.BUBBLE_POST[0], W.BUBBLE_POST[1]
+    speed = rho2 * u2 / (rho2 - rho1)
+    x0 = (w.nx // 2 + 128 + 32) * w.dx                 # initial shock plane
+    expect = x0 + speed * w.nsteps * w.dt
+    mid = 0.5 * (rho1 + rho2)
+    for row in (0, w.ny - 1):
+        r = got["rho"][row]
+        i = int(np.where(r > mid)[0][0])
+        x = (i - 0.5) * w.dx + (mid - r[i - 1]) / (r[i] - r[i - 1]) * w.dx
+        print("heavy bubble t = 0.9, wall row %d: shock at x = %.4f, Rankine-Hugoniot %.4f"
+              % (row, x, expect))
+        assert abs(x - expect) < 3 * w.dx

@@ -189,7 +189,7 @@ BUBBLE_RATES = rates(s5=1e4, s6=1e4, s7=1e4, s8=1e4)
 
 
 def shock_bubble(nx=2048, ny=1024, dx=1e-3, dt=1e-5, radius=128,
-                 bubble_rho=0.1358, nsteps=2000):
+                 bubble_rho=0.1358, nsteps=2000, s=None):
     """Mach-1.22 planar shock (post-shock gas on the right, moving left) and a
     light circular bubble in pressure equilibrium (p = 1, T = 1/rho_b), centre
     (nx/2, ny/2), shock plane ``radius + 32`` nodes to the right of the
@@ -207,7 +207,52 @@ def shock_bubble(nx=2048, ny=1024, dx=1e-3, dt=1e-5, radius=128,
     bc = (("extrap", None), ("eq", BUBBLE_POST), ("reflect", None),
           ("reflect", None))
     return Workload("shock_bubble_%dx%d" % (nx, ny), nx, ny, dx, dx, dt,
-                    BUBBLE_RATES, bc, *fields, nsteps=nsteps)
+                    BUBBLE_RATES if s is None else s, bc, *fields, nsteps=nsteps)
+
+
+# Sec. V.C, second case: a heavy bubble (rho 3.1538, p = 1), s5 = 1e3.
+HEAVY_BUBBLE_RHO = 3.1538
+HEAVY_BUBBLE_RATES = rates(s5=1e3)
+
+
+def heavy_bubble(nx=2048, ny=1024, dx=1e-3, dt=1e-5, radius=128, nsteps=2000):
+    """The shock-bubble set-up of ``shock_bubble`` with the paper's heavy
+    bubble and its rates."""
+    w = shock_bubble(nx, ny, dx, dt, radius, HEAVY_BUBBLE_RHO, nsteps, s=HEAVY_BUBBLE_RATES)
+    w.name = "heavy_bubble_%dx%d" % (nx, ny)
+    return w
+
+
+# ----------------------------------------------------------------------------
+# Mach reflection (Sec. V.B.b)
+# ----------------------------------------------------------------------------
+MACH_PRE = (2.0, 0.0, 0.0, 0.5)
+MACH_POST = (3.17647, 0.555556 * math.cos(math.pi / 6), -0.555556 * math.sin(math.pi / 6), 0.839506)
+MACH_RATES = rates(s5=1e3, s6=5e2, s7=1e3, s8=1e3)
+
+
+def mach_reflection(nx=600, ny=300, dx=0.003, dt=1e-5, nsteps=25000, foot=150):
+    """Sec. V.B.b: a Mach-1.5 planar shock (post-shock state MACH_POST behind
+    it, MACH_PRE ahead) meets a 30-degree wedge whose tip is at x = foot dx on
+    the bottom. Initially the post-shock region is y >= h(x, 0), h(x, t) =
+    tan 60 (x - foot dx) - 1.5 t / sin 30 (cell-centred nodes). Sides: left
+    held at the post-shock state; right linear extrapolation; bottom the
+    post-shock state for x <= foot dx and reflecting beyond; top the
+    post-shock state for x <= g(t) = foot dx + tan 30 (H + 1.5 t / sin 30),
+    H the domain height (0.9 in the paper), and extrapolation beyond --
+    both as split sides (reading R22)."""
+    x = (np.arange(nx)[None, :] + 0.5) * dx
+    y = (np.arange(ny)[:, None] + 0.5) * dx
+    h0 = math.tan(math.pi / 3) * (x - foot * dx)
+    post = np.broadcast_to(y >= h0, (ny, nx))
+    fields = [np.where(post, a, b) for a, b in zip(MACH_POST, MACH_PRE)]
+    H = ny * dx
+    t30 = math.tan(math.pi / 6)
+    bc = (("eq", MACH_POST), ("extrap", None),
+          ("eq", MACH_POST, ("reflect", foot * dx, 0.0)),
+          ("eq", MACH_POST, ("extrap", foot * dx + t30 * H, t30 * 1.5 / math.sin(math.pi / 6))))
+    return Workload("mach_reflection_%dx%d" % (nx, ny), nx, ny, dx, dx, dt, MACH_RATES, bc,
+                    *fields, nsteps=nsteps, meta={"foot": foot * dx, "H": H})
 
 
 # ----------------------------------------------------------------------------
@@ -288,6 +333,19 @@ def tube_batch(ntubes=4096, nx_min=128, nx_max=2048, seed=0):
             "right": np.stack([rho[:, 1], u[:, 1], np.zeros(ntubes), T[:, 1]], 1),
             "s": s}
 
+
+
+def tube_fields(B):
+    """The batch's initial (rho, u, v, T), each one array over all tubes'
+    nodes in tube order: the left state at x <= 0.5, the right beyond."""
+    fields = []
+    for q in range(4):
+        parts = []
+        for t in range(len(B["nx"])):
+            x = (np.arange(B["nx"][t]) + 0.5) / B["nx"][t]
+            parts.append(np.where(x <= 0.5, B["left"][t, q], B["right"][t, q]))
+        fields.append(np.concatenate(parts))
+    return fields
 
 # ----------------------------------------------------------------------------
 # 2D Riemann quadrant problems (learned-corrector data)
