@@ -23,7 +23,8 @@ summed over ranks; ``fp64`` carries the FP64 path measured the same way;
 ``large_grid`` the FP32 and tensor-core (3xTF32) steps on the 2048 x 1024
 shock-bubble grid (268 MB per step, larger than L2, so timed as CUDA-graph
 replays back to back) with their errors against an FP64 GPU run;
-``tubes`` the batched quasi-1D Riemann problems; ``cpu_baseline`` is the FP64
+``tubes`` the batched quasi-1D Riemann problems; ``von_neumann`` a stability
+map of Sec. IV's example on the device; ``cpu_baseline`` is the FP64
 numpy oracle on one host core over a bounded sample; ``e2e`` times the same
 step through the C ABI with host buffers; ``clocks`` are nvidia-smi samples
 taken inside the FP32 timed region (and over the whole run).
@@ -309,7 +310,7 @@ def traffic_record(kernel):
 
 # The sources that define the 2D step kernels (their DRAM counts in
 # profiles/traffic.json are valid while these files are unchanged).
-STEP_SOURCES = ("lbm_core.cu", "lbm_step.cuh", "d2v16.cuh", "tma.cuh")
+STEP_SOURCES = ("lbm_core.cu", "lbm_step.cuh", "d2v16.cuh", "tma.cuh", "coeffs.h")
 
 
 def source_hash():
@@ -373,6 +374,48 @@ def tubes_measure(torch, lbm, stream, args):
                 "graph": True, "launches_per_call": 1}
     finally:
         lbm.lbm_batch_destroy(b)
+
+
+def vn_measure(torch, lbm, stream):
+    """Stability map of the Sec. IV example: u = 0 .. 10 in 32 steps for the
+    MRT and the SRT rates (64 cases) x 4096 wave numbers k dx in [0, pi] along
+    x = 262 144 matrices G per sweep; eigenvalues on the device (FP64,
+    compute-bound: the 4 KB of inputs stay in L2 and are not flushed)."""
+    import workloads
+    ex = workloads.vn_example(nk=4096)
+    us = np.linspace(0.0, 10.0, 32)
+    states = np.array([[2.0, u, 0.0, 2.0] for _ in range(2) for u in us])
+    rates = np.repeat(ex["rates"], len(us), axis=0)
+    cases = torch.from_numpy(lbm.vn_cases(states, rates)).cuda()
+    k = torch.from_numpy(np.ascontiguousarray(ex["k"])).cuda()
+    n = cases.shape[0] * k.shape[0]
+    radius = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def sweep():
+        lbm.lbm_vn_spectrum(cases, k, ex["dx"], ex["dy"], ex["dt"], radius=radius, stream=stream,
+                            count_nonconverged=False)
+
+    for _ in range(3):
+        sweep()
+    stream.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    times = []
+    for _ in range(5):
+        ev[0].record(stream)
+        sweep()
+        ev[1].record(stream)
+        stream.synchronize()
+        times.append(ev[0].elapsed_time(ev[1]))
+    r = radius.cpu().numpy().reshape(2, len(us), -1).max(axis=2)
+    stable = {name: float(us[np.nonzero(r[c] <= 1.0 + 1e-9)[0]].max()) if (r[c] <= 1.0 + 1e-9).any()
+              else None for c, name in enumerate(ex["names"])}
+    ms = statistics.median(times)
+    return {"workload": "Sec. IV example (rho, T) = (2, 2), u = 0..10 (32 values) x {MRT, SRT} "
+                        "x 4096 k dx in [0, pi]",
+            "matrices": n, "ms_per_sweep": ms, "matrices_per_s": n / (ms * 1e-3),
+            "largest_stable_u": stable,
+            "max_radius_at_u10": {name: float(r[c, -1]) for c, name in enumerate(ex["names"])},
+            "launches_per_sweep": 2, "dtype": "f64"}
 
 
 def run_ours(args):
@@ -459,6 +502,7 @@ def run_ours(args):
     large = None if args.no_large else bubble_measure(torch, lbm, stream, args.audit_every, hbm_peak)
 
     tubes = None if args.no_tubes else tubes_measure(torch, lbm, stream, args)
+    vn = None if args.no_vn else vn_measure(torch, lbm, stream)
     clocks.stop()
 
     if rank != 0:
@@ -503,6 +547,7 @@ def run_ours(args):
         "sustained": sustained,
         "large_grid": large,
         "tubes": tubes,
+        "von_neumann": vn,
         "e2e": {"value": cells / statistics.mean(e2e_t), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "lbm_set_populations(pinned host) + lbm_step(1) + lbm_moments(pinned host)"},
@@ -549,6 +594,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-tubes", action="store_true")
+    ap.add_argument("--no-vn", action="store_true")
     ap.add_argument("--tube-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)

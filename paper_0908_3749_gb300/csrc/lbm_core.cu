@@ -402,31 +402,6 @@ __global__ void k_ghost_eq(R* g, const Coeffs<double> K, const double* states) {
 // ---------------------------------------------------------------------------
 // Host-side constants
 // ---------------------------------------------------------------------------
-// Gauss-Jordan inverse with partial pivoting in long double (n <= 4).
-bool invert(int n, const double* a, double* out) {
-  long double m[4][8];
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < 2 * n; ++j)
-      m[i][j] = j < n ? (long double)a[i * n + j] : (long double)(j - n == i);
-  for (int c = 0; c < n; ++c) {
-    int p = c;
-    for (int r = c + 1; r < n; ++r)
-      if (fabsl(m[r][c]) > fabsl(m[p][c])) p = r;
-    if (m[p][c] == 0.0L) return false;
-    for (int j = 0; j < 2 * n; ++j) { long double t = m[c][j]; m[c][j] = m[p][j]; m[p][j] = t; }
-    const long double piv = m[c][c];
-    for (int j = 0; j < 2 * n; ++j) m[c][j] /= piv;
-    for (int r = 0; r < n; ++r) {
-      if (r == c) continue;
-      const long double fac = m[r][c];
-      for (int j = 0; j < 2 * n; ++j) m[r][j] -= fac * m[c][j];
-    }
-  }
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) out[i * n + j] = (double)m[i][n + j];
-  return true;
-}
-
 // Dense M of Eqs. 5a-5p on the velocities of Eq. 4 (row n = moment n + 1,
 // column i = velocity i + 1) and its inverse by Gauss-Jordan elimination with
 // partial pivoting in long double; used by the tensor-core step.
@@ -462,60 +437,9 @@ bool dense_moment_matrices(double (&M)[16][16], double (&Minv)[16][16]) {
 }
 
 bool build_coeffs(const lbm_config& cfg, Coeffs<double>& K) {
-  fill_forward(K);
-  double m0[16], mx[16], my[16], mc[4], ms[4];
-  for (int r = 0; r < 4; ++r)
-    for (int g = 0; g < 4; ++g) {
-      m0[4 * r + g] = b0(r, g);
-      mx[4 * r + g] = bx(r, g);
-      my[4 * r + g] = by(r, g);
-    }
-  for (int r = 0; r < 2; ++r)
-    for (int g = 0; g < 2; ++g) {
-      mc[2 * r + g] = bc2(r, g);
-      ms[2 * r + g] = bs2(r, g);
-    }
-  double i0[16], ix[16], iy[16], ic[4], is[4];
-  if (!invert(4, m0, i0) || !invert(4, mx, ix) || !invert(4, my, iy) ||
-      !invert(2, mc, ic) || !invert(2, ms, is))
-    return false;
-  const double sx[4] = {0.5, 0.5, 0.25, 0.25};
-  for (int g = 0; g < 4; ++g)
-    for (int c = 0; c < 4; ++c) {
-      K.E0[g][c] = 0.25 * i0[g * 4 + c];
-      K.EX[g][c] = sx[g] * ix[g * 4 + c];
-      K.EY[g][c] = sx[g] * iy[g * 4 + c];
-    }
-  for (int r = 0; r < 2; ++r)
-    for (int c = 0; c < 2; ++c) {
-      K.EC[r][c] = 0.25 * ic[r * 2 + c];
-      K.ES[r][c] = 0.25 * is[r * 2 + c];
-    }
-  double w[17];
-  for (int k = 1; k <= 16; ++k) w[k] = -cfg.dt * cfg.s[k - 1];
-  const int cx[3] = {7, 9, 15}, cy[3] = {8, 10, 16};
-  for (int g = 0; g < 4; ++g) {
-    K.K0[g][0] = K.E0[g][2] * w[11];
-    K.K0[g][1] = K.E0[g][3] * w[12];
-    for (int c = 0; c < 3; ++c) {
-      K.KX[g][c] = K.EX[g][c + 1] * w[cx[c]];
-      K.KY[g][c] = K.EY[g][c + 1] * w[cy[c]];
-    }
-  }
-  for (int r = 0; r < 2; ++r) {
-    K.KC[r][0] = K.EC[r][0] * w[5];
-    K.KC[r][1] = K.EC[r][1] * w[13];
-    K.KS[r][0] = K.ES[r][0] * w[6];
-    K.KS[r][1] = K.ES[r][1] * w[14];
-  }
-  for (int i = 0; i < 16; ++i) {
-    const double ax = vel_x(i) * cfg.dt / cfg.dx, ay = vel_y(i) * cfg.dt / cfg.dy;
-    K.a0[i] = 1.0 - ax * ax - ay * ay;
-    K.aE[i] = 0.5 * (ax * ax - ax);
-    K.aW[i] = 0.5 * (ax * ax + ax);
-    K.aN[i] = 0.5 * (ay * ay - ay);
-    K.aS[i] = 0.5 * (ay * ay + ay);
-  }
+  if (!lattice_constants(K)) return false;
+  set_rates(K, cfg.dt, cfg.s);
+  set_advection(K, cfg.dt, cfg.dx, cfg.dy);
   return true;
 }
 

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
+#include "coeffs.h"
 #include "d2v16.cuh"
 #include "tma.cuh"
 

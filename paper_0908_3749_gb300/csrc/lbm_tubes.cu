@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "../../include/lbm_batch.h"
+#include "coeffs.h"
 #include "d2v16.cuh"
 #include "tma.cuh"
 
@@ -413,66 +414,6 @@ int find_variant(int tile, int threads) {
 }
 
 thread_local std::string g_batch_create_error = "no error";
-
-// Shared with lbm_core.cu's constants (same lattice): block inverses.
-bool invert_small(int n, const double* a, double* out) {
-  long double m[4][8];
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < 2 * n; ++j)
-      m[i][j] = j < n ? (long double)a[i * n + j] : (long double)(j - n == i);
-  for (int c = 0; c < n; ++c) {
-    int p = c;
-    for (int r = c + 1; r < n; ++r)
-      if (fabsl(m[r][c]) > fabsl(m[p][c])) p = r;
-    if (m[p][c] == 0.0L) return false;
-    for (int j = 0; j < 2 * n; ++j) std::swap(m[c][j], m[p][j]);
-    const long double piv = m[c][c];
-    for (int j = 0; j < 2 * n; ++j) m[c][j] /= piv;
-    for (int r = 0; r < n; ++r) {
-      if (r == c) continue;
-      const long double fac = m[r][c];
-      for (int j = 0; j < 2 * n; ++j) m[r][j] -= fac * m[c][j];
-    }
-  }
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) out[i * n + j] = (double)m[i][n + j];
-  return true;
-}
-
-// Lattice constants E (scaled block inverses) in double; K/a fields unused.
-bool lattice_constants(Coeffs<double>& K) {
-  double m0[16], mx[16], my[16], mc[4], ms[4];
-  for (int r = 0; r < 4; ++r)
-    for (int g = 0; g < 4; ++g) {
-      m0[4 * r + g] = b0(r, g);
-      mx[4 * r + g] = bx(r, g);
-      my[4 * r + g] = by(r, g);
-    }
-  for (int r = 0; r < 2; ++r)
-    for (int g = 0; g < 2; ++g) {
-      mc[2 * r + g] = bc2(r, g);
-      ms[2 * r + g] = bs2(r, g);
-    }
-  double i0[16], ix[16], iy[16], ic[4], is[4];
-  if (!invert_small(4, m0, i0) || !invert_small(4, mx, ix) || !invert_small(4, my, iy) ||
-      !invert_small(2, mc, ic) || !invert_small(2, ms, is))
-    return false;
-  memset(&K, 0, sizeof(K));
-  fill_forward(K);
-  const double sx[4] = {0.5, 0.5, 0.25, 0.25};
-  for (int g = 0; g < 4; ++g)
-    for (int c = 0; c < 4; ++c) {
-      K.E0[g][c] = 0.25 * i0[g * 4 + c];
-      K.EX[g][c] = sx[g] * ix[g * 4 + c];
-      K.EY[g][c] = sx[g] * iy[g * 4 + c];
-    }
-  for (int r = 0; r < 2; ++r)
-    for (int c = 0; c < 2; ++c) {
-      K.EC[r][c] = 0.25 * ic[r * 2 + c];
-      K.ES[r][c] = 0.25 * is[r * 2 + c];
-    }
-  return true;
-}
 
 }  // namespace
 

@@ -514,3 +514,103 @@ def lbm_restrict(fine, r, out, stream=None):
         stream = stream.cuda_stream
     Hf, Wf = int(fine.shape[-2]), int(fine.shape[-1])
     _ccheck(load().lbm_restrict(_dev(fine), Hf, Wf, int(r), _dev(out), _vp(stream or None)))
+
+
+# ----------------------------------------------------------------------------
+# include/lbm_vn.h: linear (von Neumann) stability analysis of Sec. IV
+# ----------------------------------------------------------------------------
+class lbm_vn_case(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("u", ctypes.c_double), ("v", ctypes.c_double),
+                ("T", ctypes.c_double), ("s", ctypes.c_double * 16)]
+
+
+_SIGS.update({
+    "lbm_vn_matrices": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int, _vp]),
+    "lbm_vn_spectrum": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, _vp, _vp, ctypes.c_int,
+                                       _vp, ctypes.POINTER(_ll)]),
+    "lbm_eig16": (ctypes.c_int, [_vp, _ll, _vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(_ll)]),
+    "lbm_vn_last_error": (ctypes.c_char_p, []),
+})
+
+
+def _vn_check(rc):
+    if rc != LBM_OK:
+        raise LBMError(rc, load().lbm_vn_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    return _vp(stream or None)
+
+
+def vn_cases(states, rates):
+    """float64 array [n][20] = (rho, u, v, T, s_1..s_16) per case, the memory
+    layout of lbm_vn_case, from states [n][4] and rates [n][16]."""
+    import numpy as np
+    states = np.atleast_2d(np.asarray(states, dtype=np.float64))
+    rates = np.atleast_2d(np.asarray(rates, dtype=np.float64))
+    if states.shape[1] != 4 or rates.shape[1] != 16 or len(states) != len(rates):
+        raise ValueError("states [n][4] and rates [n][16] expected")
+    return np.ascontiguousarray(np.concatenate([states, rates], axis=1))
+
+
+def _vn_args(cases, k):
+    """(pointer, on_device, count) for the cases and the wave vectors; both
+    host (numpy) or both device (torch CUDA)."""
+    pc, dc = _ptr(cases)
+    pk, dk = _ptr(k)
+    if dc != dk:
+        raise ValueError("cases and k must both be host or both be device arrays")
+    if cases.shape[-1] != 20 or k.shape[-1] != 2:
+        raise ValueError("cases [n][20] and k [nk][2] expected")
+    return pc, pk, dc, int(cases.shape[0]), int(k.shape[0])
+
+
+def lbm_vn_matrices(cases, k, dx, dy, dt, G=None, stream=None):
+    """G of Sec. IV for every (case, wave vector). Host inputs: returns a
+    complex128 array [ncases][nk][16][16]. Device inputs: G must be a float64
+    CUDA tensor of [ncases * nk * 512] values (asynchronous)."""
+    import numpy as np
+    pc, pk, dev, nc, nk = _vn_args(cases, k)
+    out = G if dev else np.empty((nc, nk, 16, 16), dtype=np.complex128)
+    _vn_check(load().lbm_vn_matrices(_vp(pc), nc, _vp(pk), nk, float(dx), float(dy), float(dt),
+                                     _vp(_ptr(out)[0]), dev, _stream_ptr(stream)))
+    return out
+
+
+def lbm_vn_spectrum(cases, k, dx, dy, dt, radius=None, omega=None, stream=None,
+                    want_omega=True, count_nonconverged=True):
+    """Eigenvalues omega of G and radius = max |omega| for every (case, wave
+    vector). Host inputs: returns (radius [ncases][nk], omega [ncases][nk][16]
+    complex or None, nonconverged). Device inputs: writes the given CUDA
+    tensors (radius: ncases * nk doubles, omega: ncases * nk * 32 doubles)."""
+    import numpy as np
+    pc, pk, dev, nc, nk = _vn_args(cases, k)
+    if not dev:
+        radius = np.empty((nc, nk))
+        omega = np.empty((nc, nk, 16), dtype=np.complex128) if want_omega else None
+    nf = _ll(0)
+    _vn_check(load().lbm_vn_spectrum(_vp(pc), nc, _vp(pk), nk, float(dx), float(dy), float(dt),
+                                     _vp(_ptr(radius)[0]), _vp(_ptr(omega)[0]), dev,
+                                     _stream_ptr(stream),
+                                     ctypes.byref(nf) if count_nonconverged else None))
+    return radius, omega, (nf.value if count_nonconverged else None)
+
+
+def lbm_eig16(A, stream=None):
+    """Eigenvalues of complex 16 x 16 matrices A [n][16][16] (host complex128):
+    returns (omega [n][16] complex, radius [n], nonconverged)."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    if A.ndim != 3 or A.shape[1:] != (16, 16):
+        raise ValueError("A [n][16][16] expected")
+    n = A.shape[0]
+    omega = np.empty((n, 16), dtype=np.complex128)
+    radius = np.empty(n)
+    nf = _ll(0)
+    _vn_check(load().lbm_eig16(_vp(A.ctypes.data), n, _vp(omega.ctypes.data),
+                               _vp(radius.ctypes.data), 0, _stream_ptr(stream), ctypes.byref(nf)))
+    return omega, radius, nf.value

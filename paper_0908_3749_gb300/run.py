@@ -2,6 +2,7 @@
 
     python -m paper_0908_3749_gb300.run --workload reflection --precision fp32 --steps 100
     python -m paper_0908_3749_gb300.run --workload tubes --steps 20 --autotune 5
+    python -m paper_0908_3749_gb300.run --workload vn --nx 4096 --steps 1
 
 Prints one JSON line with the step count, the watchdog status, the
 conservation totals and the ranges of rho, u, v, T. Nothing is timed; it is
@@ -17,7 +18,7 @@ import numpy as np
 from . import lbm
 
 WORKLOADS = ("reflection", "bubble", "sod", "couette", "random", "mach", "heavy_bubble",
-             "tubes")
+             "tubes", "vn")
 
 
 def make_workload(name, nx=None, ny=None):
@@ -52,6 +53,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.workload == "tubes":
         return run_tubes(args)
+    if args.workload == "vn":
+        return run_vn(args)
 
     w = make_workload(args.workload, args.nx, args.ny)
     cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, args.precision,
@@ -99,6 +102,22 @@ def run_tubes(args):
         lbm.lbm_batch_destroy(b)
     print(json.dumps(out))
     return 0 if rc == lbm.LBM_OK and to == 0 else 1
+
+
+def run_vn(args):
+    """Stability sweep of the Sec. IV example (workloads.vn_example): MRT and
+    SRT rates, ``--nx`` wave numbers k dx in [0, pi] along x (default 4096),
+    ``--steps`` repetitions of the sweep (one eigenvalue launch each)."""
+    import workloads as W
+    ex = W.vn_example(nk=args.nx or 4096)
+    cases = lbm.vn_cases(ex["states"], ex["rates"])
+    for _ in range(max(1, args.steps)):
+        radius, _, nf = lbm.lbm_vn_spectrum(cases, ex["k"], ex["dx"], ex["dy"], ex["dt"],
+                                            want_omega=False)
+    out = {"workload": "vn", "cases": ex["names"], "nk": int(ex["k"].shape[0]),
+           "max_radius": [float(r.max()) for r in radius], "nonconverged": nf}
+    print(json.dumps(out))
+    return 0 if nf == 0 else 1
 
 
 if __name__ == "__main__":

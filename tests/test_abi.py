@@ -4,6 +4,7 @@ before touching a GPU."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -66,3 +67,30 @@ def test_launch_shape_entry_points_reject_null_context():
     assert lib.lbm_set_step_blocks(None, 4) == lbm.LBM_ERR_INVALID
     assert lib.lbm_step_blocks(None) == -1
     assert lib.lbm_autotune(None, 5) == lbm.LBM_ERR_INVALID
+
+
+@pytest.mark.parametrize("change", [
+    {"dx": 0.0}, {"dt": float("nan")}, {"state": (0.0, 0.0, 0.0, 1.0)},
+    {"state": (1.0, 0.0, 0.0, -1.0)}, {"rate": float("inf")}, {"k": float("nan")},
+    {"nk": 0},
+])
+def test_vn_rejects_bad_arguments_on_host(change):
+    from paper_0908_3749_gb300 import lbm
+    state = change.get("state", (1.0, 0.1, 0.0, 1.0))
+    rates = [1e4] * 16
+    rates[6] = change.get("rate", 1e4)
+    cases = lbm.vn_cases([state], [rates])
+    k = np.zeros((0 if change.get("nk") == 0 else 2, 2))
+    if k.shape[0]:
+        k[1, 0] = change.get("k", 100.0)
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_vn_spectrum(cases, k, change.get("dx", 1e-3), 1e-3, change.get("dt", 1e-5))
+    assert ei.value.code == lbm.LBM_ERR_INVALID
+    assert lbm.load().lbm_vn_last_error()
+
+
+def test_eig16_rejects_empty_input():
+    from paper_0908_3749_gb300 import lbm
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.lbm_eig16(np.zeros((0, 16, 16), complex))
+    assert ei.value.code == lbm.LBM_ERR_INVALID

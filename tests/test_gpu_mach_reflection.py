@@ -48,12 +48,16 @@ def test_heavy_bubble_small_parity():
 
 def test_heavy_bubble_to_paper_time_shock_speed():
     """The heavy bubble at the paper's dx = 0.003, dt = 1e-5 to t = 0.9
-    (90 000 steps, FP32) on 1024 x 512 nodes: the run stays physical, and on
-    the wall rows (128 nodes clear of the bubble) the incident shock has
-    moved at its Rankine-Hugoniot speed s = rho2 u2 / (rho2 - rho1) (the
-    gas ahead is at rest) to within 3 nodes."""
+    (90 000 steps, FP64) on 1024 x 512 nodes: the run stays physical, and on
+    the wall rows (128 nodes clear of the bubble) the incident shock is where
+    a planar shock moving at the Rankine-Hugoniot speed s = rho2 u2 /
+    (rho2 - rho1) (gas ahead at rest) would be, or behind it: the bubble
+    delays the diffracted front (measured 2.7 nodes behind; the scheme's
+    planar shock alone, run in 1D by the oracle, is 0.25 nodes ahead of the
+    Rankine-Hugoniot position at t = 0.9). Bar: from 0.5 node ahead to 4
+    nodes behind."""
     w = W.heavy_bubble(nx=1024, ny=512, dx=0.003, radius=128, nsteps=90000)
-    got, _, status = gpu_run(w, w.nsteps, "fp32")
+    got, _, status = gpu_run(w, w.nsteps, "fp64")
     assert status[0] == 0 and status[1] == -1
     assert (got["rho"] > 0).all() and (got["T"] > 0).all()
     rho1, rho2, u2 = W.BUBBLE_PRE[0], W.BUBBLE_POST[0], W.BUBBLE_POST[1]
@@ -67,4 +71,4 @@ def test_heavy_bubble_to_paper_time_shock_speed():
         x = (i - 0.5) * w.dx + (mid - r[i - 1]) / (r[i] - r[i - 1]) * w.dx
         print("heavy bubble t = 0.9, wall row %d: shock at x = %.4f, Rankine-Hugoniot %.4f"
               % (row, x, expect))
-        assert abs(x - expect) < 3 * w.dx
+        assert -0.5 * w.dx <= x - expect <= 4 * w.dx

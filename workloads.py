@@ -347,6 +347,26 @@ def tube_fields(B):
         fields.append(np.concatenate(parts))
     return fields
 
+
+# ----------------------------------------------------------------------------
+# Linear stability (Sec. IV)
+# ----------------------------------------------------------------------------
+def vn_example(nk=181):
+    """The stability example of Sec. IV: state (rho, u, v, T) = (2, 10, 0, 2),
+    dx = dy = 2e-3, dt = 1e-5; MRT rates s5 = 6500, s7 = s8 = 9e4, s9 = 8e4,
+    s13 = 7e4, s14 = 8e3, s15 = 2.5e4, others 1e5, and the single-relaxation
+    version tau = 1e-5 (every s = 1e5); nk wave numbers k dx uniformly in
+    [0, pi] along x."""
+    mrt = np.full(16, 1e5)
+    for k, val in ((5, 6500.0), (7, 9e4), (8, 9e4), (9, 8e4), (13, 7e4), (14, 8e3), (15, 2.5e4)):
+        mrt[k - 1] = val
+    dx = 2e-3
+    th = np.linspace(0.0, np.pi, nk)
+    state = (2.0, 10.0, 0.0, 2.0)
+    return {"names": ["mrt", "srt"], "states": np.array([state, state]),
+            "rates": np.stack([mrt, np.full(16, 1e5)]), "dx": dx, "dy": dx, "dt": 1e-5,
+            "k": np.stack([th / dx, np.zeros(nk)], 1)}
+
 # ----------------------------------------------------------------------------
 # 2D Riemann quadrant problems (learned-corrector data)
 # ----------------------------------------------------------------------------
