@@ -26,8 +26,17 @@ constexpr unsigned long long NONE = ~0ull;
 // tiles, one node per thread (FP64-ALU-bound: small tiles spread the work
 // evenly over the SMs).
 template <typename R> struct Shape;
+// FP32 node tiles are 32 x LBM_F32_TILE_Y nodes (4, 8 or 16 rows), two rows
+// per thread; the launch bounds keep 128 registers per thread (one-tile form)
+// and 170 (persistent form, two tile stages).
+#ifndef LBM_F32_TILE_Y
+#define LBM_F32_TILE_Y 8
+#endif
 template <> struct Shape<float> {
-  static constexpr int X = 32, Y = 8, TY = 4, MINB = 4, MINB_PIPE = 3;
+  static constexpr int X = 32, Y = LBM_F32_TILE_Y, TY = Y / 2;
+  static constexpr int MINB = 512 / (X * TY);
+  static constexpr int MINB_PIPE = 384 / (X * TY) > 0 ? 384 / (X * TY) : 1;
+  static_assert(Y == 4 || Y == 8 || Y == 16, "FP32 tile rows: 4, 8 or 16");
 };
 template <> struct Shape<double> {
   static constexpr int X = 32, Y = 2, TY = 2, MINB = 8, MINB_PIPE = 6;

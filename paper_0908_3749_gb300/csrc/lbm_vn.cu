@@ -151,26 +151,31 @@ __device__ __forceinline__ cplx csqrt(cplx z) {
   const double t = sqrt(0.5 * (r - z.re));
   return mk(fabs(z.im) / (2.0 * t), copysign(t, z.im));
 }
-// Givens rotation G = [[c, s], [-conj(s), c]], c real, with G (a, b)^T = (r, 0)^T.
+// Givens rotation G = [[c, s], [-conj(s), c]], c real, with G (a, b)^T = (r, 0)^T:
+// c = |a| / n, s = (a / |a|) conj(b) / n, r = (a / |a|) n, n^2 = |a|^2 + |b|^2,
+// from two reciprocal square roots. The solver scales its matrix to entries
+// below 2 in magnitude first, so the squares cannot overflow.
 __device__ __forceinline__ void givens(cplx a, cplx b, double& c, cplx& s, cplx& r) {
-  const double aa = cabs(a), ab = cabs(b);
-  if (ab == 0.0) {
+  const double na2 = norm2(a), nb2 = norm2(b);
+  if (nb2 == 0.0) {
     c = 1.0;
     s = mk(0.0, 0.0);
     r = a;
     return;
   }
-  if (aa == 0.0) {
+  if (na2 == 0.0) {
+    const double ib = rsqrt(nb2);
     c = 0.0;
-    s = (1.0 / ab) * conj(b);
-    r = mk(ab, 0.0);
+    s = ib * conj(b);
+    r = mk(nb2 * ib, 0.0);
     return;
   }
-  const double n = hypot(aa, ab);
-  const cplx ph = (1.0 / aa) * a;
-  c = aa / n;
-  s = (1.0 / n) * (ph * conj(b));
-  r = n * ph;
+  const double n2 = na2 + nb2;
+  const double inv = rsqrt(n2), ia = rsqrt(na2);
+  const cplx ph = ia * a;  // a / |a|
+  c = na2 * ia * inv;
+  s = inv * (ph * conj(b));
+  r = (n2 * inv) * ph;
 }
 
 struct EigWork {
@@ -179,25 +184,35 @@ struct EigWork {
   cplx rs[16];     // Givens sines of the current sweep
   double rc[16];   // Givens cosines
   double norm;     // max |a_ij|_1 after the reduction
+  double scale;    // power of two the matrix was divided by
   int finite;
 };
 
 // Eigenvalues of W.A by the 16 lanes in `mask` (lane l = 0..15 of them). On
-// a true return the eigenvalues are W.A's diagonal. Every lane returns the
-// same value.
+// a true return the eigenvalues are W.A's diagonal (scaled back). Every lane
+// returns the same value.
 __device__ bool eig16(EigWork& W, int l, unsigned mask, int base) {
   constexpr double U = 2.220446049250313e-16;  // 2^-52
   __syncwarp(mask);
   if (l == 0) {
     int fin = 1;
+    double amax = 0.0;
     for (int i = 0; i < 256; ++i) {
       const cplx a = W.A[i >> 4][i & 15];
       fin &= isfinite(a.re) && isfinite(a.im);
+      amax = fmax(amax, fmax(fabs(a.re), fabs(a.im)));
     }
     W.finite = fin;
+    // 2^e with amax / 2^e in [1, 2): an exact scaling (e clamped so that
+    // 2^-e stays a normal number)
+    W.scale = (fin && amax > 0.0) ? ldexp(1.0, max(-1000, min(1000, ilogb(amax)))) : 1.0;
   }
   __syncwarp(mask);
   if (!W.finite) return false;
+  {
+    const double inv_scale = 1.0 / W.scale;  // a power of two: exact
+    for (int j = 0; j < 16; ++j) W.A[l][j] = inv_scale * W.A[l][j];
+  }
 
   // Householder reduction to upper Hessenberg form: A <- H A H, H = I - tau v v^H.
   for (int c = 0; c < 14; ++c) {
@@ -311,6 +326,8 @@ __device__ bool eig16(EigWork& W, int l, unsigned mask, int base) {
     ++its;
     ++total;
   }
+  __syncwarp(mask);
+  W.A[l][l] = W.scale * W.A[l][l];
   __syncwarp(mask);
   return true;
 }

@@ -191,3 +191,18 @@ def test_device_pointers_give_the_host_results():
     assert np.array_equal(rr.cpu().numpy().reshape(r_host.shape), r_host)
     w = ww.cpu().numpy().view(np.complex128).reshape(w_host.shape)
     assert np.array_equal(w, w_host)
+
+
+def test_eig16_power_of_two_scaling_is_exact():
+    """The solver normalises each matrix by an exact power of two, so scaling
+    the input by 2^k scales the computed eigenvalues by exactly 2^k, far into
+    the ranges where squares of the raw entries would overflow or underflow."""
+    from paper_0908_3749_gb300 import lbm
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(4, 16, 16)) + 1j * rng.normal(size=(4, 16, 16))
+    w0, r0, _ = lbm.lbm_eig16(A)
+    for k in (600, -600):
+        w, r, nf = lbm.lbm_eig16(A * 2.0 ** k)
+        assert nf == 0
+        assert np.array_equal(w, w0 * 2.0 ** k)
+        assert np.array_equal(r, r0 * 2.0 ** k)
