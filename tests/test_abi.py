@@ -41,6 +41,7 @@ def test_library_exports_every_declared_symbol():
     ({"bc0": ("eq", (1, 0, 0, 1), ("periodic", 0.0, 0.0))}, -1),      # split into periodic
     ({"bc0": ("extrap", None, ("eq", 0.0, 0.0))}, -1),               # far Dirichlet state missing
     ({"bc0": ("eq", (1, 0, 0, 1), ("reflect", float("inf"), 0.0))}, -1),
+    ({"nx": 16384, "ny": 16448, "precision": "tc_tf32x3"}, -2),     # 2^32 elements: no TC form
 ])
 def test_create_rejects_bad_configs_on_host(change, code):
     from paper_0908_3749_gb300 import lbm
