@@ -83,11 +83,12 @@ def workload():
     return W.regular_reflection()
 
 
-def config_json(w, precision, audit_every):
+def config_json(w):
+    """The workload, the same in both arms' lines; how each arm computes it is
+    in the line's ``path``."""
     return {"workload": "regular_shock_reflection_%dx%d" % (w.nx, w.ny),
             "nx": w.nx, "ny": w.ny, "dx": w.dx, "dt": w.dt, "mach": 2.9,
-            "precision": precision, "audit_every": audit_every,
-            "l2": "flushed between timed steps (256 MiB write + 256 MiB read)"}
+            "l2": "GPU arm: flushed between timed steps (256 MiB write + 256 MiB read)"}
 
 
 # ----------------------------------------------------------------------------
@@ -528,7 +529,9 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": dict(config_json(w, "fp32", args.audit_every), step_blocks=blocks32),
+        "config": config_json(w),
+        "path": {"precision": "fp32", "audit_every": args.audit_every, "step_blocks": blocks32,
+                 "kernel": "k_step<float> (one block per 32 x 8 node tile)"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": gbs / hbm_peak, "traffic": traffic_record("k_step<float>"),
                      "kernel": "k_step<float>",
@@ -576,7 +579,8 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n,
         "warmup": args.warmup, "ms_per_step": el / n * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_json(w, "fp64", 0), "impl": "reference",
+        "config": config_json(w), "impl": "reference",
+        "path": {"precision": "fp64", "audit_every": 0, "kernel": "numpy oracle, one host thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "%d full-grid steps of the FP64 numpy oracle, 1 thread" % n},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
