@@ -204,23 +204,26 @@ def whole_job_rate(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
-def time_steps(torch, lbm, ctx, stream, flush, K, W):
-    """Per-step CUDA-event times (ms) of K steps after W warm-up steps."""
+def time_steps(torch, lbm, ctx, stream, flush, K, W, per=1):
+    """Per-step CUDA-event times (ms) of K steps after W warm-up steps, timed
+    in iterations of `per` steps (one lbm_step call each; the L2 is flushed
+    between iterations). Each iteration's time is listed once per step it
+    advanced, divided by `per`."""
     with torch.cuda.stream(stream):
         for _ in range(W):
-            lbm.lbm_step(ctx, 1)
+            lbm.lbm_step(ctx, per)
             flush()
         stream.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(K)]
+              for _ in range(K // per)]
         torch.cuda._sleep(200_000_000)   # keep the GPU busy while the loop is enqueued
         for a, b in ev:
             a.record(stream)
-            lbm.lbm_step(ctx, 1)
+            lbm.lbm_step(ctx, per)
             b.record(stream)
             flush()
         stream.synchronize()
-    return [a.elapsed_time(b) for a, b in ev]
+    return [a.elapsed_time(b) / per for a, b in ev for _ in range(per)]
 
 
 def time_graph_steps(torch, lbm, ctx, stream, n, reps):
@@ -254,9 +257,9 @@ def field_error(lbm, ctx, ref):
 
 def bubble_measure(torch, lbm, stream, audit_every, hbm_peak):
     """The 2048 x 1024 shock-bubble grid (268 MB of FP32 traffic per step,
-    larger than L2): FP32 and tensor-core (3xTF32) steps timed as back-to-back
-    graph replays, and both compared with an FP64 GPU run after the same
-    number of steps."""
+    larger than L2): FP32, tensor-core (3xTF32) and two-steps-per-launch FP32
+    steps timed as back-to-back graph replays, each compared with an FP64 GPU
+    run after the same number of steps."""
     import workloads
     wl = workloads.shock_bubble()
     cl = wl.nx * wl.ny
@@ -268,14 +271,19 @@ def bubble_measure(torch, lbm, stream, audit_every, hbm_peak):
     ref = [np.empty((wl.ny, wl.nx)) for _ in range(4)]
     lbm.lbm_moments(c64, *ref)
     lbm.lbm_destroy(c64)
-    for prec, key in (("fp32", "fp32"), ("tc_tf32x3", "tensor_core_tf32x3")):
-        ctx = make_ctx(lbm, wl, prec, 0, stream)
+    for prec, key, fused in (("fp32", "fp32", False), ("tc_tf32x3", "tensor_core_tf32x3", False),
+                             ("fp32", "fp32_two_steps_per_launch", True)):
+        ctx = make_ctx(lbm, wl, prec, 0, stream, tune=not fused)
         try:
+            if fused:
+                lbm.lbm_set_fused_steps(ctx, 2)
             lbm.lbm_step(ctx, nsteps)
             err = field_error(lbm, ctx, ref)
             st = lbm.lbm_status(ctx)
-            ctx2 = make_ctx(lbm, wl, prec, audit_every, stream)
+            ctx2 = make_ctx(lbm, wl, prec, audit_every, stream, tune=not fused)
             try:
+                if fused:
+                    lbm.lbm_set_fused_steps(ctx2, 2)
                 ms = time_graph_steps(torch, lbm, ctx2, stream, 64, 10)
                 blocks = lbm.lbm_step_blocks(ctx2)
             finally:
@@ -286,6 +294,10 @@ def bubble_measure(torch, lbm, stream, audit_every, hbm_peak):
         out[key] = {"value": cl / (ms * 1e-3), "ms_per_step": ms, "achieved_gbs": gbs,
                     "frac_of_hbm": gbs / hbm_peak, "step_blocks": blocks,
                     "error_vs_fp64_gpu_after_%d_steps" % nsteps: err, "status": list(st)}
+        if fused:
+            out[key]["note"] = ("two time steps per launch (temporal blocking): the populations "
+                                "cross HBM once per two steps, so achieved_gbs counts the "
+                                "single-step algorithmic 128 B per node-update")
     return out
 
 

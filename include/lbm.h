@@ -181,18 +181,19 @@ int lbm_set_populations(lbm_ctx* ctx, const void* f, long long step, int on_devi
 /* Bytes per population element (8 or 4) of ctx. */
 int lbm_element_size(lbm_ctx* ctx);
 
-/* Launch shape of the step (LBM_FP64 / LBM_FP32). A step is one persistent
- * launch of `blocks` thread blocks that share the grid's node tiles (32 x 8
- * nodes in FP32, 32 x 4 in FP64) through a device-side counter. Results do
- * not depend on it (each node's update is the same, audit partials are kept
- * per tile); only the speed does.
- *  lbm_set_step_blocks: 0 = the default (as many blocks as fit on the
- *    device at once, at most one per tile); larger values are capped at the
- *    number of tiles. Synchronises; LBM_ERR_UNSUPPORTED for LBM_TC_TF32X3
- *    (one CTA per 128-node tile).
+/* Launch shape of the step (LBM_FP64 / LBM_FP32). The grid is cut into node
+ * tiles (32 x 8 nodes in FP32, 32 x 2 in FP64). With one block per tile each
+ * block updates its tile; with fewer blocks each block takes tiles b, b + G,
+ * b + 2G, ... (G blocks), copying its next tile into shared memory while it
+ * computes the current one. Results do not depend on it (each node's update
+ * is the same, audit partials are kept per tile); only the speed does.
+ *  lbm_set_step_blocks: 0 = the default, one block per tile; larger values
+ *    are capped at the number of tiles. Synchronises; LBM_ERR_UNSUPPORTED
+ *    for LBM_TC_TF32X3 (one CTA per 128-node tile).
  *  lbm_step_blocks: the current value (-1 for a NULL ctx).
- *  lbm_autotune: times `launches` step launches for each of 1, 2, ... blocks
- *    per multiprocessor and keeps the fastest. The timed launches read the
+ *  lbm_autotune: times `launches` step launches for each candidate (one
+ *    block per tile; 1 .. k blocks per multiprocessor; ceil(tiles / m) blocks
+ *    for m = 2 .. 8) and keeps the fastest. The timed launches read the
  *    current populations and write the spare buffer against scratch
  *    counters: the state, the step count, the watchdog and the audit log are
  *    unchanged. Call it after lbm_set_init / lbm_set_populations.
@@ -200,6 +201,23 @@ int lbm_element_size(lbm_ctx* ctx);
 int lbm_set_step_blocks(lbm_ctx* ctx, int blocks);
 int lbm_step_blocks(lbm_ctx* ctx);
 int lbm_autotune(lbm_ctx* ctx, int launches);
+
+/* Time steps per launch of the FP32 step (LBM_FP32 only): 1 (default) or 2.
+ * With 2, lbm_step advances two time levels per launch: each block loads its
+ * 32 x 8 tile with a halo of two rows and four columns, computes level n + 1
+ * on the tile and a one-node ring around it in shared memory (the ring is
+ * computed again by the neighbouring tiles), then level n + 2 on the tile,
+ * and stores only that (temporal blocking: one read and one write of the
+ * populations per two steps). Each node update is the one-step arithmetic
+ * (the ring nodes in unpaired FP32, so results can differ from single steps
+ * in the last bit); the watchdog checks both levels and audits use the same
+ * fixed-order reductions. Odd step counts end with a single step; contexts
+ * with audit_every = 1 always take single steps.
+ *  lbm_set_fused_steps: LBM_ERR_INVALID for other values,
+ *    LBM_ERR_UNSUPPORTED for LBM_FP64 and LBM_TC_TF32X3 contexts.
+ *  lbm_fused_steps: the current value (-1 for a NULL ctx). */
+int lbm_set_fused_steps(lbm_ctx* ctx, int steps_per_launch);
+int lbm_fused_steps(lbm_ctx* ctx);
 
 /* One-line description of the last error on ctx (or of the last lbm_create
  * failure on this thread when ctx is NULL). Never NULL. */

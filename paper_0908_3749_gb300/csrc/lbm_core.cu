@@ -208,8 +208,15 @@ __device__ __forceinline__ void step_any(const StepArgs<R>& A, const R* __restri
     step_tile_x2<Off>(A, fin, fout, stage, cur, audit, t, sm, bad, negT);
 }
 
+// Blocks per SM the one-tile form is compiled for: the FP32 form with 64-bit
+// offsets needs more than 128 registers (it spilled at 4 blocks per SM).
 template <typename R, typename Off>
-__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB)
+constexpr int step_minb() {
+  return (sizeof(R) == 4 && sizeof(Off) == 8) ? Shape<R>::MINB - 1 : Shape<R>::MINB;
+}
+
+template <typename R, typename Off>
+__global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, (step_minb<R, Off>()))
     k_step(const __grid_constant__ CUtensorMap tmap, const R* __restrict__ fin,
            R* __restrict__ fout, const StepArgs<R> A) {
   constexpr int N = Shape<R>::X * Shape<R>::TY;
@@ -483,6 +490,9 @@ struct lbm_ctx {
   unsigned char* tc_b = nullptr;  // TF32 parts of M and M^-1 (4 KB)
   float* tc_w = nullptr;          // -dt s_k, 0 for the conserved k
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int fuse = 1;                   // time steps per FP32 launch (1 or 2)
+  CUtensorMap tmap2[2];           // two-step kernel: tile + two-row halo
+  cudaGraphExec_t graph2[2] = {nullptr, nullptr};  // GRAPH_CHUNK steps, two per launch
   std::string err = "no error";
 };
 
@@ -596,6 +606,33 @@ int ensure_graph(lbm_ctx* c, int from) {
   return LBM_OK;
 }
 
+// Two time steps in one launch (FP32, one block per tile).
+int launch_fused(lbm_ctx* c, cudaStream_t s, int from) {
+  StepArgs<float> A = make_args<float>(c, from);
+  A.nblocks = c->ntiles;
+  CK(c, fused_launch(c->tmap2[from], (const float*)c->f[from], (float*)c->f[1 - from], A, c->wide, s));
+  return LBM_OK;
+}
+
+int ensure_graph2(lbm_ctx* c, int from) {
+  if (c->graph2[from]) return LBM_OK;
+  cudaGraph_t g;
+  CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int f = from, rc = LBM_OK;
+  for (int k = 0; k < GRAPH_CHUNK / 2 && rc == LBM_OK; ++k) {
+    rc = launch_fused(c, c->stream, f);
+    f = 1 - f;
+  }
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (rc != LBM_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->graph2[from], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+  return LBM_OK;
+}
+static_assert(GRAPH_CHUNK % 4 == 0, "graphs of fused launches leave the buffer parity unchanged");
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -614,24 +651,33 @@ EncodeTiledFn tensor_map_encoder() {
   return fn;
 }
 
-// Tensor map of one population buffer: dims (pitch, ny, 16), box = one tile
-// with its halo.
-int encode_tile_map(lbm_ctx* c, int b) {
+// Tensor map of population buffer b: dims (pitch, ny, 16), box = one tile
+// with its halo (`rows` rows, Tile<R>::BXP columns, 16 populations).
+int encode_map(lbm_ctx* c, int b, cuuint32_t rows, CUtensorMap* out) {
   EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return fail(c, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   const bool dbl = c->esize == 8;
   const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->cfg.ny, 16};
   const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->esize, (cuuint64_t)c->plane * c->esize};
-  const cuuint32_t rows = c->tc ? (cuuint32_t)(TC_Y + 2)
-                                : (cuuint32_t)(dbl ? Tile<double>::ROWS : Tile<float>::ROWS);
   const cuuint32_t box[3] = {(cuuint32_t)(dbl ? Tile<double>::BXP : Tile<float>::BXP), rows, 16};
   const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = enc(&c->tmap[b], dbl ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+  const CUresult r = enc(out, dbl ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                          3, c->f[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(c, LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return LBM_OK;
+}
+
+// The step kernels' maps of buffer b (and, for FP32, the two-step kernel's).
+int encode_tile_map(lbm_ctx* c, int b) {
+  const bool dbl = c->esize == 8;
+  const cuuint32_t rows = c->tc ? (cuuint32_t)(TC_Y + 2)
+                                : (cuuint32_t)(dbl ? Tile<double>::ROWS : Tile<float>::ROWS);
+  int rc = encode_map(c, b, rows, &c->tmap[b]);
+  if (rc == LBM_OK && !dbl && !c->tc)
+    rc = encode_map(c, b, (cuuint32_t)fused_halo_rows(), &c->tmap2[b]);
+  return rc;
 }
 
 // Resets the status block for time level `step` in slot `cur` (a kernel, so
@@ -773,6 +819,7 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
     c->nblocks = default_blocks(c);
     c->grid = dim3(c->nblocks);
     if (e == cudaSuccess) e = c->esize == 8 ? allow_pipe_smem<double>() : allow_pipe_smem<float>();
+    if (e == cudaSuccess && c->esize == 4) e = fused_prepare();
   }
   const int npartial = std::max(c->ntiles, (int)(c->aux_grid.x * c->aux_grid.y));
   const size_t fbytes = (size_t)16 * c->plane * c->esize;
@@ -870,6 +917,19 @@ int lbm_set_init(lbm_ctx* c, const double* rho, const double* u, const double* v
 int lbm_step(lbm_ctx* c, long long nsteps) {
   if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
   if (nsteps < 0) return fail(c, LBM_ERR_INVALID, "nsteps < 0");
+  if (c->fuse == 2 && c->cfg.audit_every != 1) {
+    while (nsteps >= GRAPH_CHUNK) {
+      int rc = ensure_graph2(c, c->cur);
+      if (rc != LBM_OK) return rc;
+      CK(c, cudaGraphLaunch(c->graph2[c->cur], c->stream));
+      nsteps -= GRAPH_CHUNK;
+    }
+    for (; nsteps >= 2; nsteps -= 2) {
+      int rc = launch_fused(c, c->stream, c->cur);
+      if (rc != LBM_OK) return rc;
+      c->cur = 1 - c->cur;
+    }
+  }
   while (nsteps >= GRAPH_CHUNK) {
     int rc = ensure_graph(c, c->cur);
     if (rc != LBM_OK) return rc;
@@ -915,6 +975,7 @@ int lbm_destroy(lbm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (int k = 0; k < 2; ++k) {
     if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+    if (c->graph2[k]) cudaGraphExecDestroy(c->graph2[k]);
     if (c->f[k]) cudaFree(c->f[k]);
   }
   if (c->geq) cudaFree(c->geq);
@@ -1100,6 +1161,17 @@ int lbm_set_step_blocks(lbm_ctx* c, int blocks) {
 }
 
 int lbm_step_blocks(lbm_ctx* c) { return c ? c->nblocks : -1; }
+
+int lbm_set_fused_steps(lbm_ctx* c, int steps) {
+  if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
+  if (steps != 1 && steps != 2) return fail(c, LBM_ERR_INVALID, "steps per launch must be 1 or 2");
+  if (steps == 2 && (c->tc || c->esize != 4))
+    return fail(c, LBM_ERR_UNSUPPORTED, "two steps per launch: LBM_FP32 contexts only");
+  c->fuse = steps;
+  return LBM_OK;
+}
+
+int lbm_fused_steps(lbm_ctx* c) { return c ? c->fuse : -1; }
 
 int lbm_autotune(lbm_ctx* c, int launches) {
   if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");

@@ -173,13 +173,11 @@ __device__ __forceinline__ int side_kind(const StepArgs<R>& A, int side, int alo
 }
 
 // Ghost populations of boundary kind `kind` outside `side` of the node with
-// conserved moments `own`. `inward` is the index of the next node inwards
-// (EXTRAP), `has_inward` false when the grid is one node deep in that
-// direction.
-template <typename R, typename Off>
-__device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict__ fin,
-                                      Off plane, int side, int kind, Cons<R> own, Off inward,
-                                      bool has_inward, R g[16]) {
+// conserved moments `own`. `inward()` gives the conserved moments of the next
+// node inwards (EXTRAP only; called only for that kind).
+template <typename R, typename InFn>
+__device__ __forceinline__ void ghost_with(const StepArgs<R>& A, int side, int kind, Cons<R> own,
+                                           InFn inward, R g[16]) {
   if (kind == LBM_BC_EQ) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) g[i] = A.geq[side * 16 + i];
@@ -196,7 +194,7 @@ __device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict_
   } else if (kind == LBM_BC_OUTFLOW) {
     // the adjacent node's state unchanged
   } else {  // LBM_BC_EXTRAP
-    const Cons<R> in = has_inward ? load_cons(A.K, fin, plane, inward) : own;
+    const Cons<R> in = inward();
     const R r1 = recip(own.rho), r2 = recip(in.rho);
     const R u1 = own.jx * r1, v1 = own.jy * r1, u2 = in.jx * r2, v2 = in.jy * r2;
     const R T1 = own.e * r1 - R(0.5) * (u1 * u1 + v1 * v1);
@@ -212,6 +210,16 @@ __device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict_
     s.e = rho * T + R(0.5) * rho * (u * u + v * v);
   }
   feq(A.K, s.rho, s.jx, s.jy, s.e, g);
+}
+
+// ghost_with whose inward node is element `inward` of the global population
+// buffer (`has_inward` false when the grid is one node deep that way).
+template <typename R, typename Off>
+__device__ __forceinline__ void ghost(const StepArgs<R>& A, const R* __restrict__ fin,
+                                      Off plane, int side, int kind, Cons<R> own, Off inward,
+                                      bool has_inward, R g[16]) {
+  ghost_with(A, side, kind, own,
+             [&]() { return has_inward ? load_cons(A.K, fin, plane, inward) : own; }, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,5 +423,14 @@ void tc_prepare_constants(const double (&M)[16][16], const double (&Minv)[16][16
 cudaError_t tc_launch(const CUtensorMap& tm, const float* fin, float* fout,
                       const StepArgs<float>& A, const unsigned char* bconst, const float* wk,
                       dim3 grid, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Two steps per launch (lbm_fused.cu)
+// ---------------------------------------------------------------------------
+size_t fused_smem_bytes();
+int fused_halo_rows();  // rows of the fused kernel's tile copy (tensor-map box)
+cudaError_t fused_prepare();
+cudaError_t fused_launch(const CUtensorMap& tm, const float* fin, float* fout,
+                         const StepArgs<float>& A, bool wide, cudaStream_t s);
 
 }  // namespace lbmk

@@ -286,7 +286,18 @@ _SIGS.update({
     "lbm_audit_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ll,
                                          ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "lbm_audit_noalloc_last_error": (ctypes.c_char_p, []),
+    "lbm_set_fused_steps": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "lbm_fused_steps": (ctypes.c_int, [_vp]),
 })
+
+
+def lbm_set_fused_steps(ctx, steps_per_launch):
+    """Time steps per FP32 launch: 1 or 2 (temporal blocking)."""
+    _check(load().lbm_set_fused_steps(ctx, int(steps_per_launch)), ctx)
+
+
+def lbm_fused_steps(ctx):
+    return int(load().lbm_fused_steps(ctx))
 NOALLOC_MAX_BLOCKS = 4096
 
 
