@@ -92,14 +92,7 @@ def test_tube_batch_full_size_sampled():
     n = 30
     b = lbm.lbm_batch_create(B["nx"], B["dx"], B["dt"], B["s"], B["left"], B["right"])
     try:
-        fields = []
-        for q in range(4):
-            parts = []
-            for t in range(nt):
-                x = (np.arange(B["nx"][t]) + 0.5) / B["nx"][t]
-                parts.append(np.where(x <= 0.5, B["left"][t, q], B["right"][t, q]))
-            fields.append(np.concatenate(parts))
-        lbm.lbm_batch_set_init(b, *fields)
+        lbm.lbm_batch_set_init(b, *W.tube_fields(B))
         lbm.lbm_batch_autotune(b, 5, None)
         lbm.lbm_batch_step(b, n)
         tot = lbm.lbm_batch_total_nodes(b)

@@ -42,12 +42,7 @@ def _batch(nx, seed=0, rates=None, dt=1e-5):
 
 
 def _fields(B):
-    out = []
-    for t in range(len(B["nx"])):
-        x = (np.arange(B["nx"][t]) + 0.5) / B["nx"][t]
-        m = x <= 0.5
-        out.append([np.where(m, B["left"][t, q], B["right"][t, q]) for q in range(4)])
-    return [np.concatenate([o[q] for o in out]) for q in range(4)]
+    return W.tube_fields(B)
 
 
 def _tube_workload(B, t):
