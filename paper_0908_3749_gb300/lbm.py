@@ -166,7 +166,12 @@ def lbm_create(cfg, stream=None):
 
 
 def lbm_set_init(ctx, rho, u, v, T):
-    ps = [_ptr(a) for a in (rho, u, v, T)]
+    """f = f^eq(rho, u, v, T): four [ny][nx] fields, all host arrays
+    (converted to C-contiguous float64) or all CUDA float64 tensors."""
+    import numpy as np
+    fields = [a if hasattr(a, "data_ptr") else np.ascontiguousarray(a, dtype=np.float64)
+              for a in (rho, u, v, T)]
+    ps = [_ptr(a) for a in fields]
     dev = {d for _, d in ps}
     if len(dev) != 1:
         raise ValueError("fields must all be host arrays or all device tensors")
