@@ -178,11 +178,11 @@ def main(argv=None):
     ap.add_argument("--ratio", type=int, default=4, help="fine / coarse resolution")
     ap.add_argument("--t-end", type=float, default=0.02)
     ap.add_argument("--dt", type=float, default=1e-5, help="coarse time step (fine: dt / ratio)")
-    ap.add_argument("--train", type=int, default=24, help="training seeds 1 .. train")
+    ap.add_argument("--train", type=int, default=64, help="training seeds 1 .. train")
     ap.add_argument("--test", type=int, default=8, help="held-out seeds 10001 .. 10000 + test")
-    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--epochs", type=int, default=150)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--loss", choices=("l1", "mse"), default="l1")
+    ap.add_argument("--loss", choices=("l1", "mse"), default="mse")
     args = ap.parse_args(argv)
 
     t0 = time.perf_counter()
