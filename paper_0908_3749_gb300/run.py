@@ -48,6 +48,8 @@ def main(argv=None):
     ap.add_argument("--audit-every", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0,
                     help="step launch blocks (0: one per tile); see lbm_set_step_blocks")
+    ap.add_argument("--fused", type=int, default=1, choices=(1, 2),
+                    help="time steps per FP32 launch (lbm_set_fused_steps)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="if > 0, choose the launch shape with lbm_autotune(launches)")
     args = ap.parse_args(argv)
@@ -66,6 +68,8 @@ def main(argv=None):
             lbm.lbm_set_step_blocks(ctx, args.blocks)
         if args.autotune > 0:
             lbm.lbm_autotune(ctx, args.autotune)
+        if args.fused == 2:
+            lbm.lbm_set_fused_steps(ctx, 2)
         lbm.lbm_step(ctx, args.steps)
         rc, bad, neg = lbm.lbm_status(ctx)
         m = [np.empty((w.ny, w.nx)) for _ in range(4)]
