@@ -45,7 +45,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-if "--impl" in sys.argv and "reference" in sys.argv or "--cpu-sample" in sys.argv:
+if ("--impl" in sys.argv and "reference" in sys.argv or "--cpu-sample" in sys.argv
+        or "--cpu-sample-tubes" in sys.argv):
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
 
@@ -108,6 +109,47 @@ def oracle_steps(seconds=None, steps=None):
         el = time.perf_counter() - t0
         if (steps is not None and n >= steps) or (seconds is not None and el >= seconds):
             return n, el
+
+
+def oracle_tube_steps(seconds):
+    """Times oracle steps of a seeded 64-tube subset of the tube batch (each
+    tube a one-node-deep grid, stepped in turn); returns (node-updates,
+    seconds)."""
+    import workloads
+    from oracle import scheme
+    B = workloads.tube_batch()
+    pick = np.random.default_rng(64).choice(len(B["nx"]), 64, replace=False)
+    tubes = []
+    for t in pick:
+        n = int(B["nx"][t])
+        x = (np.arange(n) + 0.5) / n
+        fields = [np.where(x <= 0.5, B["left"][t, q], B["right"][t, q])[None, :] for q in range(4)]
+        bc = (("eq", tuple(B["left"][t])), ("eq", tuple(B["right"][t])),
+              ("periodic", None), ("periodic", None))
+        w = workloads.Workload("tube", n, 1, B["dx"][t], B["dx"][t], B["dt"], tuple(B["s"][t]), bc,
+                               *fields)
+        tubes.append([scheme.init_populations(*w.fields()), w.cfg(), n])
+    updates, t0 = 0, time.perf_counter()
+    while True:
+        for tb in tubes:
+            tb[0] = scheme.step(tb[0], tb[1])
+            updates += tb[2]
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return updates, el
+
+
+def tubes_cpu_baseline(seconds):
+    """oracle_tube_steps in a fresh single-threaded process."""
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-tubes",
+                          str(seconds)], capture_output=True, text=True, timeout=600)
+    if res.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + res.stderr[-200:]}
+    n, el = json.loads(res.stdout.strip().splitlines()[-1])
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d node-updates of a seeded 64-tube subset, FP64 numpy oracle (%.1f s, 1 thread)"
+                      % (n, el)}
 
 
 def cpu_baseline(seconds):
@@ -571,6 +613,8 @@ def run_ours(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if tubes:
+            tubes["cpu_baseline"] = tubes_cpu_baseline(min(args.cpu_seconds, 6.0))
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -614,9 +658,13 @@ def main():
     ap.add_argument("--tube-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-sample-tubes", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_sample is not None:
         print(json.dumps(oracle_steps(seconds=args.cpu_sample)))
+        return
+    if args.cpu_sample_tubes is not None:
+        print(json.dumps(oracle_tube_steps(args.cpu_sample_tubes)))
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
