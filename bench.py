@@ -381,9 +381,9 @@ def e2e_steps(torch, lbm, ctx, w, K, W):
     populations in from pinned host memory, runs one step and reads the
     moments back into pinned host memory. Wall-clock seconds per step."""
     f = torch.empty((16, w.ny, w.nx), dtype=torch.float32).pin_memory()
-    outs = [torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    outs = torch.empty((4, w.ny, w.nx), dtype=torch.float64).pin_memory()  # rho, u, v, T
     fn = f.numpy()
-    on = [o.numpy() for o in outs]
+    on = list(outs.numpy())
     lbm.lbm_get_populations(ctx, fn)
     times = []
     for k in range(W + K):
@@ -393,7 +393,7 @@ def e2e_steps(torch, lbm, ctx, w, K, W):
         lbm.lbm_moments(ctx, *on)
         if k >= W:
             times.append(time.perf_counter() - t0)
-    return times, f.numel() * 4, sum(o.numel() * 8 for o in outs)
+    return times, f.numel() * 4, outs.numel() * 8
 
 
 def tubes_measure(torch, lbm, stream, args):

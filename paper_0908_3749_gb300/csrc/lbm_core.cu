@@ -962,9 +962,16 @@ int lbm_moments(lbm_ctx* c, double* rho, double* u, double* v, double* T, int on
                                                       c->pitch, c->plane, c->Kd);
   CK(c, cudaGetLastError());
   if (!on_device) {
-    for (int k = 0; k < 4; ++k)
-      if (h[k])
-        CK(c, cudaMemcpyAsync(h[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    // Four host fields that are consecutive blocks of one array come back in
+    // one copy (the staging blocks are consecutive too).
+    const bool one = h[0] && h[1] == h[0] + n && h[2] == h[1] + n && h[3] == h[2] + n;
+    if (one) {
+      CK(c, cudaMemcpyAsync(h[0], d[0], 4 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    } else {
+      for (int k = 0; k < 4; ++k)
+        if (h[k])
+          CK(c, cudaMemcpyAsync(h[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
     CK(c, cudaStreamSynchronize(c->stream));
   }
   return LBM_OK;

@@ -183,3 +183,23 @@ def test_couette_paper_case1_velocity_error():
     ue = exact.couette_u(y, w.nsteps * w.dt, 0.1, w.meta["D"], 1.0 / 1e5, 1.0)
     E = exact.relative_error(np.r_[-0.1, u, 0.1], np.r_[-0.1, ue, 0.1])
     assert abs(E - 0.0702) < 0.1 * 0.0702, E
+
+
+def test_moments_into_one_host_array_equal_separate_arrays():
+    """lbm_moments with the four fields as consecutive blocks of one host
+    array (one device-to-host copy) gives what four separate arrays get."""
+    from paper_0908_3749_gb300 import lbm
+    w = W.random_state(45, 13, seed=8)
+    cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, "fp64", 0)
+    ctx = lbm.lbm_create(cfg)
+    try:
+        lbm.lbm_set_init(ctx, *w.fields())
+        lbm.lbm_step(ctx, 7)
+        block = np.empty((4, w.ny, w.nx))
+        lbm.lbm_moments(ctx, *block)
+        sep = [np.empty((w.ny, w.nx)) for _ in range(4)]
+        lbm.lbm_moments(ctx, *sep)
+    finally:
+        lbm.lbm_destroy(ctx)
+    for k in range(4):
+        assert np.array_equal(block[k], sep[k])
