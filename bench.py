@@ -363,9 +363,10 @@ def traffic_record(kernel):
     return rec["dram_bytes_per_launch"] if rec.get("source_hash") == source_hash() else None
 
 
-# The sources that define the 2D step kernels (their DRAM counts in
-# profiles/traffic.json are valid while these files are unchanged).
-STEP_SOURCES = ("lbm_core.cu", "lbm_step.cuh", "d2v16.cuh", "tma.cuh", "coeffs.h")
+# The sources that define the one-step grid kernels (their DRAM counts in
+# profiles/traffic.json are valid while these files are unchanged; host code
+# that launches them is not among them).
+STEP_SOURCES = ("lbm_step_kernels.cuh", "lbm_step.cuh", "d2v16.cuh", "tma.cuh", "coeffs.h")
 
 
 def source_hash():
