@@ -81,3 +81,27 @@ def test_heavy_slab_transmitted_and_reflected_shocks():
     e_r = (x_r - (xf + SR * (t - t_hit))) / DX
     print("transmitted shock %.2f nodes, reflected shock %.2f nodes from exact" % (e_t, e_r))
     assert abs(e_t) <= 1.5 and abs(e_r) <= 1.5
+
+
+def test_linear_extrapolation_side_amplifies_noise_at_rest():
+    """Gas at rest (rho = 1, T = 1) with 1e-7 noise, the heavy bubble's rates
+    and sides: the left side's linear extrapolation (reading R7) amplifies the
+    noise next to it, the zero-gradient outflow side does not (after 3000
+    steps: measured 2.1e-6 against 4.1e-7). Over 60 000 steps the growth
+    reaches 7e-2 (about 2e-4 per step), which is how FP32 rounding noise, but
+    not FP64's, turns the long heavy-bubble run unphysical at that side."""
+    n = 48
+    rng = np.random.default_rng(0)
+    fields = [1.0 + 1e-7 * rng.standard_normal((n, n)), 1e-7 * rng.standard_normal((n, n)),
+              1e-7 * rng.standard_normal((n, n)), 1.0 + 1e-7 * rng.standard_normal((n, n))]
+    dev = {}
+    for left in ("extrap", "outflow"):
+        bc = ((left, None), ("eq", W.BUBBLE_PRE), ("reflect", None), ("reflect", None))
+        w = W.Workload("rest", n, n, DX, DX, DT, W.HEAVY_BUBBLE_RATES, bc, *fields)
+        f, bad = scheme.run(scheme.init_populations(*w.fields()), w.cfg(), 3000)
+        T = scheme.macroscopic(f)[3]
+        dev[left] = float(np.abs(T - 1.0).max())
+        assert bad is None
+    print("max |T - 1| after 3000 steps: %s" % dev)
+    assert dev["extrap"] > 3.0 * dev["outflow"]
+    assert dev["outflow"] < 1e-6
