@@ -490,7 +490,7 @@ int vn_run(const lbm_vn_case* cases, int ncases, const double* k, int nk, double
   }
   cudaStream_t s = (cudaStream_t)stream;
   DevBuf bc, bk, bj, bg, br, bo, bf;
-  const void *dcases, *dk;
+  const void *dcases = nullptr, *dk = nullptr;
   if ((rc = stage_in(cases, sizeof(lbm_vn_case) * ncases, on_device, s, bc, &dcases)) ||
       (rc = stage_in(k, sizeof(double) * 2 * nk, on_device, s, bk, &dk)))
     return rc;
@@ -552,7 +552,7 @@ int lbm_eig16(const double* A, long long n, double* omega, double* radius, int o
   if ((n + MPB - 1) / MPB > 0x7FFFFFFFLL) return vfail(LBM_ERR_INVALID, "too many matrices");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   DevBuf ba, bo, br, bf;
-  const void* dA;
+  const void* dA = nullptr;
   int rc;
   if ((rc = stage_in(A, sizeof(double) * 512 * (size_t)n, on_device, s, ba, &dA))) return rc;
   void *dw = nullptr, *dr = nullptr;
