@@ -15,19 +15,23 @@ L2 and no dirty lines left to write back. Each timed step
 is bracketed by CUDA events on the launching stream; the GPU is kept busy
 while the host enqueues the loop, so host launch latency is not timed.
 
-Each context's launch shape is chosen first with lbm_autotune (a timing of
-the candidate block counts that leaves the state untouched).
+The timed per-step runs use the library's default launch (one block per
+tile), the fastest in that regime; the long-run figures (``sustained``,
+``large_grid``) choose the launch shape with lbm_autotune (a timing of the
+candidate block counts that leaves the state untouched).
 
 Lines printed (rank 0): one JSON object. ``value`` is FP32-path cell-updates/s
 summed over ranks; ``fp64`` carries the FP64 path measured the same way;
-``large_grid`` the FP32 and tensor-core (3xTF32) steps on the 2048 x 1024
-shock-bubble grid (268 MB per step, larger than L2, so timed as CUDA-graph
-replays back to back) with their errors against an FP64 GPU run;
-``tubes`` the batched quasi-1D Riemann problems; ``von_neumann`` a stability
-map of Sec. IV's example on the device; ``cpu_baseline`` is the FP64
-numpy oracle on one host core over a bounded sample; ``e2e`` times the same
-step through the C ABI with host buffers; ``clocks`` are nvidia-smi samples
-taken inside the FP32 timed region (and over the whole run).
+``sustained`` the same grid as a long run issues it (graph replays, L2 not
+flushed); ``large_grid`` the FP32, tensor-core (3xTF32) and two-steps-per-
+launch FP32 steps on the 2048 x 1024 shock-bubble grid (268 MB per step,
+larger than L2, so timed as CUDA-graph replays back to back) with their
+errors against an FP64 GPU run; ``tubes`` the batched quasi-1D Riemann
+problems, with a CPU oracle baseline on a 64-tube subset; ``von_neumann`` a
+stability map of Sec. IV's example on the device; ``cpu_baseline`` is the
+FP64 numpy oracle on one host core over a bounded sample; ``e2e`` times the
+same step through the C ABI with host buffers; ``clocks`` are nvidia-smi
+samples taken inside the FP32 timed region (and over the whole run).
 
 ``--impl reference`` times the CPU oracle instead (the only reference
 implementation this method has), on the same workload, rank 0 only.
