@@ -1,5 +1,7 @@
-// lbm_core.cu -- 2D grid path of the MRT-FD D2V16 scheme: kernels and the C ABI
-// declared in include/lbm.h.
+// lbm_core.cu -- 2D grid path of the MRT-FD D2V16 scheme: the launches of the
+// step kernels (lbm_step_kernels.cuh; two steps per launch: lbm_fused.cu),
+// the auxiliary kernels (initial state, moments, audit, Dirichlet ghosts,
+// status, repitch) and the C ABI declared in include/lbm.h.
 //
 // Data layout in HBM: populations are structure-of-arrays,
 //   f[i][y][x] at offset i * plane + y * pitch + x,
