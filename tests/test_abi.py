@@ -95,3 +95,35 @@ def test_eig16_rejects_empty_input():
     with pytest.raises(lbm.LBMError) as ei:
         lbm.lbm_eig16(np.zeros((0, 16, 16), complex))
     assert ei.value.code == lbm.LBM_ERR_INVALID
+
+
+def _build_c_example(tmp_path):
+    """Compiles tests/abi_example.c as C99 against include/ and links it to
+    the library; returns (executable, environment)."""
+    import shutil
+    import subprocess
+    from paper_0908_3749_gb300 import build, lbm
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    lbm.load()
+    exe = str(tmp_path / "abi_example")
+    res = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                          "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_example.c"),
+                          "-L", build.OUT, "-llbm", "-lm", "-o", exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    env = dict(os.environ, LD_LIBRARY_PATH=build.OUT + os.pathsep + os.environ.get("LD_LIBRARY_PATH", ""))
+    return exe, env
+
+
+def test_headers_are_c_and_a_c_program_links(tmp_path):
+    """The ABI is plain C: a C99 program using only include/lbm.h compiles
+    with -pedantic -Werror and links against the library. Without a GPU it
+    must fail with an error status and a message, not crash."""
+    import subprocess
+    exe, env = _build_c_example(tmp_path)
+    import torch
+    if torch.cuda.is_available():
+        return  # run by the GPU test
+    res = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=60)
+    assert res.returncode == 1 and "lbm_create failed" in res.stderr, (res.returncode, res.stderr)

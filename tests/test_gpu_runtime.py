@@ -203,3 +203,14 @@ def test_moments_into_one_host_array_equal_separate_arrays():
         lbm.lbm_destroy(ctx)
     for k in range(4):
         assert np.array_equal(block[k], sep[k])
+
+
+def test_c_program_on_the_abi(tmp_path):
+    """tests/abi_example.c, built with gcc against include/lbm.h and the
+    library, runs 200 FP64 steps on a periodic grid and checks conservation
+    and the watchdog by itself."""
+    import subprocess
+    from test_abi import _build_c_example
+    exe, env = _build_c_example(tmp_path)
+    res = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=120)
+    assert res.returncode == 0 and "abi example ok" in res.stdout, (res.returncode, res.stderr)
