@@ -1,40 +1,42 @@
 #!/usr/bin/env python
 """Throughput of the fused D2V16 MRT-FD step on GB300.
 
-Workload: the 2D regular shock reflection (Sec. V.B.a geometry) on a 600 x 200
-grid, dx = dy = 1e-3, dt = 2e-6: Mach-2.9 inflow (rho = 1, T = 1) on the left,
-the oblique-shock post-shock state held on the top, a reflecting lower wall
-and linear extrapolation on the right. One benchmark step is one time step of
-the whole hot path (boundary ghosts, moments, equilibria, relaxation,
-back-map, Lax-Wendroff update, watchdog and conservation audit) over the grid.
+Headline workload: the shock-bubble interaction of Sec. V.C on a 2048 x 1024
+grid (dx = dy = 1e-3, dt = 1e-5): a Mach-1.22 planar shock (gamma = 2
+post-shock state (1.28, -0.3774, 0, p = 1.6512) held on the right) running
+into a light circular bubble (rho = 0.1358, p = 1, radius 128 nodes) in gas
+at rest, reflecting top and bottom, linear extrapolation on the left. One
+benchmark step is one time step of the whole hot path over the grid (boundary
+ghosts, moments, Eq. 14 equilibria, relaxation, back-map, Lax-Wendroff update
+of Eq. A.1, watchdog and, every ``--audit-every`` steps, the conservation
+audit), in the paper's arithmetic: FP64.
 
-The grid (15 MB in FP32) fits in the 129 MB L2, so the L2 is flushed between
-timed steps, outside the timed events: a 256 MiB write followed by a 256 MiB
-read of another buffer, so that each timed step starts with the grid out of
-L2 and no dirty lines left to write back. Each timed step
-is bracketed by CUDA events on the launching stream; the GPU is kept busy
-while the host enqueues the loop, so host launch latency is not timed.
+Timing: the K timed steps follow W warm-up steps and are bracketed by CUDA
+events on the launching stream, with a barrier and a device synchronisation
+on both sides; the job's time is the maximum over ranks. Each FP64
+population buffer is 268 MB, twice the 129 MB L2, so consecutive steps do
+not find their inputs in L2 (no flush is needed). The FP64 step is bound by
+the FP64 units, not by memory: its roofline is arithmetic ("alu"), against
+the FP64 fused multiply-add rate measured in this run
+(include/lbm_probe.h), with the HBM fraction beside it.
 
-The timed per-step runs use the library's default launch (one block per
-tile), the fastest in that regime; the long-run figures (``sustained``,
-``large_grid``) choose the launch shape with lbm_autotune (a timing of the
-candidate block counts that leaves the state untouched).
-
-Lines printed (rank 0): one JSON object. ``value`` is FP32-path cell-updates/s
-summed over ranks; ``fp64`` carries the FP64 path measured the same way;
-``sustained`` the same grid as a long run issues it (graph replays, L2 not
-flushed); ``large_grid`` the FP32, tensor-core (3xTF32) and two-steps-per-
-launch FP32 steps on the 2048 x 1024 shock-bubble grid (268 MB per step,
-larger than L2, so timed as CUDA-graph replays back to back) with their
-errors against an FP64 GPU run; ``tubes`` the batched quasi-1D Riemann
-problems, with a CPU oracle baseline on a 64-tube subset; ``von_neumann`` a
-stability map of Sec. IV's example on the device; ``cpu_baseline`` is the
-FP64 numpy oracle on one host core over a bounded sample; ``e2e`` times the
-same step through the C ABI with host buffers; ``clocks`` are nvidia-smi
-samples taken inside the FP32 timed region (and over the whole run).
+Lines printed (rank 0): one JSON object. Besides the contract keys:
+``fp32_large_grid``, ``tensor_core_tf32x3`` and
+``fp32_two_steps_per_launch`` are the reduced-precision steps on the same
+grid (64-step CUDA-graph replays back to back) with their errors against an
+FP64 GPU run; ``reflection_600x200`` the 600 x 200 regular shock reflection
+(Sec. V.B.a geometry) in FP64 and FP32, each step timed alone with the L2
+flushed before it, and as a long run (graph replays, L2-resident);
+``tubes`` the batch of 4096 quasi-1D Riemann problems (stable and unstable
+tubes counted apart); ``von_neumann`` a stability map of Sec. IV's example;
+``peaks`` the measured FMA rates; ``cpu_baseline`` the FP64 numpy oracle on
+the host cores (all cores, and one) over a bounded sample of the headline
+workload; ``e2e`` the headline step through the C ABI with host buffers;
+``clocks`` nvidia-smi samples around the headline's timed region.
 
 ``--impl reference`` times the CPU oracle instead (the only reference
-implementation this method has), on the same workload, rank 0 only.
+implementation this method has) on the same workload, on all host cores,
+rank 0 only.
 """
 import argparse
 import hashlib
@@ -49,8 +51,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-if ("--impl" in sys.argv and "reference" in sys.argv or "--cpu-sample" in sys.argv
-        or "--cpu-sample-tubes" in sys.argv):
+if "--cpu-sample" in sys.argv or "--cpu-sample-tubes" in sys.argv:
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
 
@@ -65,7 +66,6 @@ BYTES_PER_CELL = {"fp64": 256, "fp32": 128}
 # transform 28, conserved moments 24, equilibria 40, deviations 77,
 # back-map 64, inverse transform 28, Lax-Wendroff update 128.
 FLOPS_PER_CELL = 389
-FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal)
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -85,34 +85,95 @@ class L2Flush:
 
 def workload():
     import workloads as W
-    return W.regular_reflection()
+    return W.shock_bubble()
 
 
 def config_json(w):
-    """The workload, the same in both arms' lines; how each arm computes it is
+    """The workload, the same in both arms' lines; how an arm computes it is
     in the line's ``path``."""
-    return {"workload": "regular_shock_reflection_%dx%d" % (w.nx, w.ny),
-            "nx": w.nx, "ny": w.ny, "dx": w.dx, "dt": w.dt, "mach": 2.9,
-            "l2": "GPU arm: flushed between timed steps (256 MiB write + 256 MiB read)"}
+    return {"workload": "shock_bubble_%dx%d" % (w.nx, w.ny),
+            "nx": w.nx, "ny": w.ny, "dx": w.dx, "dt": w.dt, "shock_mach": 1.22,
+            "bubble_rho": 0.1358, "bubble_radius_nodes": 128,
+            "l2": "inputs larger than L2: 268 MB per FP64 population buffer (L2 129 MB), "
+                  "no flush"}
 
 
 # ----------------------------------------------------------------------------
 # CPU oracle timing
 # ----------------------------------------------------------------------------
-def oracle_steps(seconds=None, steps=None):
-    """Times oracle steps on the workload; returns (steps, seconds)."""
-    from oracle import scheme
+def slab_workload(k, nslabs):
+    """Rows [k h, (k+1) h) of the headline grid (h = ny / nslabs, the last
+    slab taking the remainder) as a grid of its own with the full grid's
+    sides (reflecting top and bottom): one host core's share of a sample."""
+    import workloads as W
     w = workload()
+    h = w.ny // nslabs
+    y0, y1 = k * h, (w.ny if k == nslabs - 1 else (k + 1) * h)
+    f = [np.ascontiguousarray(a[y0:y1]) for a in w.fields()]
+    return W.Workload(w.name + "_slab", w.nx, y1 - y0, w.dx, w.dy, w.dt, w.s, w.bc, *f)
+
+
+def oracle_steps(k, nslabs, seconds=None, steps=None, warmup=0):
+    """Times oracle steps of slab k of nslabs; returns (cells, steps, seconds)."""
+    from oracle import scheme
+    w = slab_workload(k, nslabs)
     f = scheme.init_populations(*w.fields())
     cfg = w.cfg()
-    f = scheme.step(f, cfg)
+    for _ in range(max(1, warmup)):   # the first step also builds the oracle's matrices
+        f = scheme.step(f, cfg)
     n, t0 = 0, time.perf_counter()
     while True:
         f = scheme.step(f, cfg)
         n += 1
         el = time.perf_counter() - t0
         if (steps is not None and n >= steps) or (seconds is not None and el >= seconds):
-            return n, el
+            return w.nx * w.ny, n, el
+
+
+def _run_slabs(nslabs, seconds=None, steps=None, warmup=1):
+    """Runs oracle_steps on nslabs host processes at once (fresh
+    single-threaded interpreters, started by fork + exec: no GPU state is
+    inherited); returns the list of (cells, steps, seconds)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    args = []
+    if seconds is not None:
+        args += ["--cpu-seconds", str(seconds)]
+    if steps is not None:
+        args += ["--steps", str(steps)]
+    procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(k),
+                               str(nslabs), "--warmup", str(warmup)] + args,
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+             for k in range(nslabs)]
+    out = []
+    for p in procs:
+        so, se = p.communicate(timeout=900)
+        if p.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + se[-300:])
+        out.append(tuple(json.loads(so.strip().splitlines()[-1])))
+    return out
+
+
+def cpu_baseline(seconds):
+    """The FP64 numpy oracle on the host: one process per core, each
+    stepping one horizontal slab of the headline grid for about ``seconds``
+    (aggregate rate), and one process stepping the whole grid (one core)."""
+    cores = os.cpu_count() or 1
+    try:
+        res = _run_slabs(cores, seconds=seconds)
+        value = sum(c * n / el for c, n, el in res)
+        one = _run_slabs(1, seconds=seconds)[0]
+    except (RuntimeError, subprocess.TimeoutExpired, ValueError) as e:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": "failed: %s" % e}
+    w = workload()
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d host processes, one per core, each stepping one %d-row slab of the "
+                      "%dx%d grid as a grid of its own (FP64 numpy oracle, %.0f s each, %d to %d "
+                      "steps per slab)" % (cores, w.ny // cores, w.nx, w.ny, seconds,
+                                           min(n for _, n, _ in res), max(n for _, n, _ in res)),
+            "single_core": {"value": one[0] * one[1] / one[2], "cores": 1,
+                            "sample": "%d steps of the whole %dx%d grid, one process (%.1f s)"
+                                      % (one[1], w.nx, w.ny, one[2])}}
 
 
 def oracle_tube_steps(seconds):
@@ -145,8 +206,9 @@ def oracle_tube_steps(seconds):
 
 def tubes_cpu_baseline(seconds):
     """oracle_tube_steps in a fresh single-threaded process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-tubes",
-                          str(seconds)], capture_output=True, text=True, timeout=600)
+                          str(seconds)], capture_output=True, text=True, timeout=600, env=env)
     if res.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": "failed: " + res.stderr[-200:]}
@@ -154,20 +216,6 @@ def tubes_cpu_baseline(seconds):
     return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d node-updates of a seeded 64-tube subset, FP64 numpy oracle (%.1f s, 1 thread)"
                       % (n, el)}
-
-
-def cpu_baseline(seconds):
-    """Runs the oracle in a fresh single-threaded process (no GPU state)."""
-    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(seconds)],
-                         capture_output=True, text=True, timeout=600)
-    if res.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": "failed: " + res.stderr[-200:]}
-    n, el = json.loads(res.stdout.strip().splitlines()[-1])
-    w = workload()
-    return {"value": w.nx * w.ny * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d FP64 numpy oracle steps of the %dx%d grid (%.1f s, 1 thread)"
-                      % (n, w.nx, w.ny, el)}
 
 
 # ----------------------------------------------------------------------------
@@ -301,23 +349,31 @@ def field_error(lbm, ctx, ref):
             "T": float(np.abs(m[3] - ref[3]).max() / np.abs(ref[3]).max())}
 
 
-def bubble_measure(torch, lbm, stream, audit_every, hbm_peak):
-    """The 2048 x 1024 shock-bubble grid (268 MB of FP32 traffic per step,
-    larger than L2): FP32, tensor-core (3xTF32) and two-steps-per-launch FP32
-    steps timed as back-to-back graph replays, each compared with an FP64 GPU
-    run after the same number of steps."""
-    import workloads
-    wl = workloads.shock_bubble()
+def make_ctx(lbm, w, precision, audit_every, stream, tune=True):
+    cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, precision, audit_every)
+    ctx = lbm.lbm_create(cfg, stream)
+    lbm.lbm_set_init(ctx, *[np.ascontiguousarray(a) for a in w.fields()])
+    if tune:
+        lbm.lbm_autotune(ctx, 20)
+    return ctx
+
+
+def large_grid_measure(torch, lbm, stream, audit_every, hbm_peak):
+    """The reduced-precision steps on the headline grid (268 MB of FP32
+    traffic per step, larger than L2): FP32, tensor-core (3xTF32) and
+    two-steps-per-launch FP32 steps timed as back-to-back graph replays, each
+    compared with an FP64 GPU run after the same number of steps."""
+    wl = workload()
     cl = wl.nx * wl.ny
-    out = {"workload": "shock_bubble_%dx%d" % (wl.nx, wl.ny), "unit": UNIT,
-           "timing": "64-step CUDA-graph replays back to back (inputs larger than L2)"}
+    out = {}
     nsteps = 256
     c64 = make_ctx(lbm, wl, "fp64", 0, stream)
     lbm.lbm_step(c64, nsteps)
     ref = [np.empty((wl.ny, wl.nx)) for _ in range(4)]
     lbm.lbm_moments(c64, *ref)
     lbm.lbm_destroy(c64)
-    for prec, key, fused in (("fp32", "fp32", False), ("tc_tf32x3", "tensor_core_tf32x3", False),
+    for prec, key, fused in (("fp32", "fp32_large_grid", False),
+                             ("tc_tf32x3", "tensor_core_tf32x3", False),
                              ("fp32", "fp32_two_steps_per_launch", True)):
         ctx = make_ctx(lbm, wl, prec, 0, stream, tune=not fused)
         try:
@@ -337,8 +393,10 @@ def bubble_measure(torch, lbm, stream, audit_every, hbm_peak):
         finally:
             lbm.lbm_destroy(ctx)
         gbs = BYTES_PER_CELL["fp32"] * cl / (ms * 1e-3) / 1e9
-        out[key] = {"value": cl / (ms * 1e-3), "ms_per_step": ms, "achieved_gbs": gbs,
+        out[key] = {"workload": "shock_bubble_%dx%d" % (wl.nx, wl.ny), "value": cl / (ms * 1e-3),
+                    "unit": UNIT, "ms_per_step": ms, "achieved_gbs": gbs,
                     "frac_of_hbm": gbs / hbm_peak, "step_blocks": blocks,
+                    "timing": "64-step CUDA-graph replays back to back (inputs larger than L2)",
                     "error_vs_fp64_gpu_after_%d_steps" % nsteps: err, "status": list(st)}
         if fused:
             out[key]["note"] = ("two time steps per launch (temporal blocking): the populations "
@@ -347,13 +405,36 @@ def bubble_measure(torch, lbm, stream, audit_every, hbm_peak):
     return out
 
 
-def make_ctx(lbm, w, precision, audit_every, stream, tune=True):
-    cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, precision, audit_every)
-    ctx = lbm.lbm_create(cfg, stream)
-    lbm.lbm_set_init(ctx, *[np.ascontiguousarray(a) for a in w.fields()])
-    if tune:
-        lbm.lbm_autotune(ctx, 20)
-    return ctx
+def reflection_measure(torch, lbm, stream, flush, audit_every, hbm_peak, K, W):
+    """The 600 x 200 regular shock reflection (15 MB in FP32, smaller than
+    L2): each step timed alone with the L2 flushed before it (the latency of
+    a cold one-wave launch), and as a long run issues it (autotuned launch,
+    64-step graph replays back to back, L2-resident)."""
+    import workloads
+    w = workloads.regular_reflection()
+    cells = w.nx * w.ny
+    out = {"workload": "regular_shock_reflection_%dx%d" % (w.nx, w.ny), "unit": UNIT,
+           "flushed": "each step timed alone, L2 flushed (256 MiB write + 256 MiB read) before it"}
+    for prec in ("fp32", "fp64"):
+        ctx = make_ctx(lbm, w, prec, audit_every, stream, tune=False)
+        try:
+            t = time_steps(torch, lbm, ctx, stream, flush, K, W)
+            ms = sum(t) / K
+            out[prec + "_flushed"] = {"value": cells / (ms * 1e-3), "ms_per_step": ms,
+                                      "step_blocks": lbm.lbm_step_blocks(ctx),
+                                      "status": list(lbm.lbm_status(ctx))}
+        finally:
+            lbm.lbm_destroy(ctx)
+        ctx = make_ctx(lbm, w, prec, audit_every, stream)
+        try:
+            ms = time_graph_steps(torch, lbm, ctx, stream, 640, 5)
+            out[prec + "_long_run"] = {"value": cells / (ms * 1e-3), "ms_per_step": ms,
+                                       "step_blocks": lbm.lbm_step_blocks(ctx)}
+        finally:
+            lbm.lbm_destroy(ctx)
+    out["fp32_flushed"]["hbm_frac"] = (BYTES_PER_CELL["fp32"] * cells
+                                       / (out["fp32_flushed"]["ms_per_step"] * 1e-3) / 1e9 / hbm_peak)
+    return out
 
 
 def traffic_record(kernel):
@@ -385,7 +466,8 @@ def e2e_steps(torch, lbm, ctx, w, K, W):
     """Steps through the C ABI with host buffers: each step copies the
     populations in from pinned host memory, runs one step and reads the
     moments back into pinned host memory. Wall-clock seconds per step."""
-    f = torch.empty((16, w.ny, w.nx), dtype=torch.float32).pin_memory()
+    es = lbm.lbm_element_size(ctx)
+    f = torch.empty((16, w.ny, w.nx), dtype=torch.float64 if es == 8 else torch.float32).pin_memory()
     outs = torch.empty((4, w.ny, w.nx), dtype=torch.float64).pin_memory()  # rho, u, v, T
     fn = f.numpy()
     on = list(outs.numpy())
@@ -398,16 +480,20 @@ def e2e_steps(torch, lbm, ctx, w, K, W):
         lbm.lbm_moments(ctx, *on)
         if k >= W:
             times.append(time.perf_counter() - t0)
-    return times, f.numel() * 4, outs.numel() * 8
+    return times, f.numel() * f.element_size(), outs.numel() * 8
 
 
-def tubes_measure(torch, lbm, stream, args):
+def tubes_measure(torch, lbm, stream, args, hbm_peak):
     """4096 seeded quasi-1D Riemann problems (Nx ~ U[128, 2048]) in one
     persistent launch per call: the autotuned tiling, then timed calls of
-    ``--tube-steps`` steps each (inputs larger than L2)."""
+    ``--tube-steps`` steps each (inputs larger than L2). The watchdog's
+    per-tube status after the timed calls splits the tubes into stable and
+    unstable ones; a second batch then runs the configuration's whole 10 000
+    steps (t = 0.1) and is counted the same way."""
     import workloads
     B = workloads.tube_batch()
     nt = len(B["nx"])
+    nx = np.asarray(B["nx"])
     b = lbm.lbm_batch_create(B["nx"], B["dx"], B["dt"], B["s"], B["left"], B["right"], stream)
     try:
         lbm.lbm_batch_set_init(b, *workloads.tube_fields(B))
@@ -415,7 +501,7 @@ def tubes_measure(torch, lbm, stream, args):
         n = args.tube_steps
         lbm.lbm_batch_step(b, n)               # capture + warm-up
         torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         times = []
         with torch.cuda.stream(stream):
             for k in range(3):
@@ -424,16 +510,35 @@ def tubes_measure(torch, lbm, stream, args):
                 ev[1].record(stream)
                 stream.synchronize()
                 times.append(ev[0].elapsed_time(ev[1]))
+        steps_run = lbm.lbm_batch_step_count(b)
         rc, bad, nbad, to = lbm.lbm_batch_status(b, nt)
         total = lbm.lbm_batch_total_nodes(b)
-        ms = min(times) / n
-        return {"workload": "4096_tubes_nx_128_2048", "nodes": total, "steps_per_launch": n,
-                "value": total / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-                "achieved_gbs": BYTES_PER_CELL["fp32"] * total / (ms * 1e-3) / 1e9,
-                "tiling": list(chosen), "unstable_tubes": nbad, "timeout": to,
-                "graph": True, "launches_per_call": 1}
     finally:
         lbm.lbm_batch_destroy(b)
+    ms = min(times) / n
+    stable_nodes = int(nx[bad < 0].sum())
+    out = {"workload": "4096_tubes_nx_128_2048", "nodes": total, "steps_per_launch": n,
+           "value": total / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+           "achieved_gbs": BYTES_PER_CELL["fp32"] * total / (ms * 1e-3) / 1e9,
+           "frac_of_hbm": BYTES_PER_CELL["fp32"] * total / (ms * 1e-3) / 1e9 / hbm_peak,
+           "tiling": list(chosen), "timeout": to, "graph": True, "launches_per_call": 1,
+           "steps_run": steps_run, "unstable_tubes": nbad, "stable_tubes": nt - nbad,
+           "value_stable": stable_nodes / (ms * 1e-3),
+           "value_stable_note": "node-updates of the tubes that stayed physical, per second of "
+                                "the whole batch's step"}
+    # the configuration's whole run, counted
+    b = lbm.lbm_batch_create(B["nx"], B["dx"], B["dt"], B["s"], B["left"], B["right"], stream)
+    try:
+        lbm.lbm_batch_set_init(b, *workloads.tube_fields(B))
+        lbm.lbm_batch_set_tiling(b, chosen[0], chosen[1])
+        lbm.lbm_batch_step(b, B["nsteps"])
+        rc, bad, nbad, to = lbm.lbm_batch_status(b, nt)
+        out["full_run"] = {"steps": B["nsteps"], "unstable_tubes": nbad, "stable_tubes": nt - nbad,
+                           "unstable_by_step": {str(s): int(((bad >= 0) & (bad <= s)).sum())
+                                                for s in (100, 1000, 10000)}}
+    finally:
+        lbm.lbm_batch_destroy(b)
+    return out
 
 
 def vn_measure(torch, lbm, stream):
@@ -478,6 +583,15 @@ def vn_measure(torch, lbm, stream):
             "launches_per_sweep": 2, "dtype": "f64"}
 
 
+def measure_peaks(lbm, stream):
+    """FMA rates of this device (lane operations per second), measured now."""
+    return {"fp64_fma_per_s": lbm.lbm_probe_fma_rate("fp64", 50.0, stream),
+            "fp32_fma_per_s": lbm.lbm_probe_fma_rate("fp32", 50.0, stream),
+            "fp32x2_fma_per_s": lbm.lbm_probe_fma_rate("fp32x2", 50.0, stream),
+            "how": "independent FMA chains (8 per thread, 4 x 256 threads per SM), best of 3 "
+                   "launches of ~50 ms (include/lbm_probe.h)"}
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -493,75 +607,45 @@ def run_ours(args):
     w = workload()
     cells = w.nx * w.ny
     stream = torch.cuda.Stream()
-    flush = L2Flush(torch)
     clocks = Clocks(device_uuid(torch))
-    # The timed per-step runs use the library's default launch (one block per
-    # tile): lbm_autotune times steps back to back with a warm L2, the regime
-    # of a long run (reported below as "sustained"), not flushed single steps.
-    ctx32 = make_ctx(lbm, w, "fp32", args.audit_every, stream, tune=False)
-    ctx64 = make_ctx(lbm, w, "fp64", args.audit_every, stream, tune=False)
     K, W = args.steps, args.warmup
-
-    # FP64 path (not the headline; measured first, same procedure)
-    t64 = time_steps(torch, lbm, ctx64, stream, flush, K, W)
-
-    # FP32 path: the timed region of the JSON line
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    h0 = time.perf_counter()
-    t32 = time_steps(torch, lbm, ctx32, stream, flush, K, W)
-    torch.cuda.synchronize()
-    h1 = time.perf_counter()
-    if dist:
-        dist.barrier()
-    blocks32, blocks64 = lbm.lbm_step_blocks(ctx32), lbm.lbm_step_blocks(ctx64)
-    total32, total64 = max_over_ranks(dist, [sum(t32), sum(t64)], "cuda")
-
-    # accuracy of the FP32 path against the FP64 path after the same steps
-    m32 = [np.empty((w.ny, w.nx)) for _ in range(4)]
-    m64 = [np.empty((w.ny, w.nx)) for _ in range(4)]
-    lbm.lbm_moments(ctx32, *m32)
-    lbm.lbm_moments(ctx64, *m64)
-    speed = np.sqrt(m64[1] ** 2 + m64[2] ** 2).max()
-    acc = {"rho": float(np.abs(m32[0] - m64[0]).max() / np.abs(m64[0]).max()),
-           "u": float(np.abs(m32[1] - m64[1]).max() / speed),
-           "v": float(np.abs(m32[2] - m64[2]).max() / speed),
-           "T": float(np.abs(m32[3] - m64[3]).max() / np.abs(m64[3]).max())}
-    s32 = lbm.lbm_status(ctx32)
-    s64 = lbm.lbm_status(ctx64)
-
-    e2e_t, h2d, d2h = e2e_steps(torch, lbm, ctx32, w, max(10, K // 4), 3)
-    lbm.lbm_destroy(ctx32)
-    lbm.lbm_destroy(ctx64)
-
-    # The same grid in a long run: autotuned launch shape, 64-step CUDA-graph
-    # replays back to back, no flush (the 15 MB grid stays in L2 between
-    # consecutive steps, as it does in a real run of this size).
-    sustained = {}
-    for prec in ("fp32", "fp64"):
-        ctx = make_ctx(lbm, w, prec, args.audit_every, stream)
-        try:
-            ms = time_graph_steps(torch, lbm, ctx, stream, 640, 5)
-            sustained[prec] = {"value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-                               "step_blocks": lbm.lbm_step_blocks(ctx)}
-        finally:
-            lbm.lbm_destroy(ctx)
-    sustained["timing"] = ("autotuned launch, 640 steps per timed call as CUDA-graph replays "
-                           "back to back, L2 not flushed (grid resident in L2)")
-
-    peaks = {}
+    peaks_file = {}
     try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peaks_file = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_peak = peaks_file.get("hbm_gbs", 6800.0)
 
-    # FP32 and tensor-core steps on a grid larger than L2 (the 2048 x 1024
-    # shock-bubble set-up): the HBM-bound regime, errors against FP64.
-    large = None if args.no_large else bubble_measure(torch, lbm, stream, args.audit_every, hbm_peak)
+    # Headline: FP64 step on the 2048 x 1024 grid. The launch shape is
+    # autotuned first (timed launches that leave the state untouched).
+    ctx = make_ctx(lbm, w, "fp64", args.audit_every, stream)
+    blocks = lbm.lbm_step_blocks(ctx)
+    peaks = measure_peaks(lbm, stream)     # the FP64 units at full clock before the region
+    with torch.cuda.stream(stream):
+        lbm.lbm_step(ctx, W)
+        stream.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        ev0.record(stream)
+        lbm.lbm_step(ctx, K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        h1 = time.perf_counter()
+        if dist:
+            dist.barrier()
+    total_ms = max_over_ranks(dist, [ev0.elapsed_time(ev1)], "cuda")[0]
+    status = lbm.lbm_status(ctx)
+    e2e_t, h2d, d2h = e2e_steps(torch, lbm, ctx, w, max(3, K // 4), 2)
+    lbm.lbm_destroy(ctx)
 
-    tubes = None if args.no_tubes else tubes_measure(torch, lbm, stream, args)
+    flush = L2Flush(torch)
+    large = None if args.no_large else large_grid_measure(torch, lbm, stream, args.audit_every, hbm_peak)
+    refl = None if args.no_small else reflection_measure(torch, lbm, stream, flush, args.audit_every,
+                                                         hbm_peak, max(K, 20), W)
+    tubes = None if args.no_tubes else tubes_measure(torch, lbm, stream, args, hbm_peak)
     vn = None if args.no_vn else vn_measure(torch, lbm, stream)
     clocks.stop()
 
@@ -569,53 +653,51 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return
-    ms32 = total32 / K
-    ms64 = total64 / K
-    gbs = BYTES_PER_CELL["fp32"] * cells / (ms32 * 1e-3) / 1e9
-    if tubes:
-        tubes["frac_of_hbm"] = tubes["achieved_gbs"] / hbm_peak
-    tflops64 = FLOPS_PER_CELL * cells / (ms64 * 1e-3) / 1e12
+    ms = total_ms / K
+    tflops = FLOPS_PER_CELL * cells / (ms * 1e-3) / 1e12
+    peak_tflops = 2.0 * peaks["fp64_fma_per_s"] / 1e12
     line = {
         "metric": METRIC,
-        "value": whole_job_rate(world, cells * K, total32 * 1e-3),
+        "value": whole_job_rate(world, cells * K, total_ms * 1e-3),
         "unit": UNIT,
         "n_gpus": world,
         "steps": K,
         "warmup": W,
-        "ms_per_step": ms32,
+        "ms_per_step": ms,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f64",
         "data": "synthetic",
         "config": config_json(w),
-        "path": {"precision": "fp32", "audit_every": args.audit_every, "step_blocks": blocks32,
-                 "kernel": "k_step<float> (one block per 32 x 8 node tile)"},
-        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": gbs / hbm_peak, "traffic": traffic_record("k_step<float>"),
-                     "kernel": "k_step<float>",
-                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                     "bytes_per_cell_update": BYTES_PER_CELL["fp32"]},
-        "accuracy_fp32_vs_fp64": acc,
-        "fp64": {"value": whole_job_rate(world, cells * K, total64 * 1e-3), "unit": UNIT,
-                 "ms_per_step": ms64, "dtype": "f64", "step_blocks": blocks64,
-                 "roofline": {"bound": "alu", "achieved": tflops64, "peak": FP64_PEAK_TFLOPS,
-                              "unit": "TFLOP/s", "frac": tflops64 / FP64_PEAK_TFLOPS,
-                              "peak_source": "nominal FP64 rate (2 DFMA/clk/SM)",
-                              "flops_per_cell_update": FLOPS_PER_CELL,
-                              "traffic": traffic_record("k_step<double>"),
-                              "hbm_frac": BYTES_PER_CELL["fp64"] * cells / (ms64 * 1e-3) / 1e9 / hbm_peak}},
-        "status": {"fp32": list(s32), "fp64": list(s64)},
-        "sustained": sustained,
-        "large_grid": large,
-        "tubes": tubes,
-        "von_neumann": vn,
+        "path": {"precision": "fp64", "audit_every": args.audit_every, "step_blocks": blocks,
+                 "kernel": "k_step<double> (32 x 2 node tiles)",
+                 "timing": "CUDA events around the K steps on the launching stream"},
+        "roofline": {"bound": "alu", "achieved": tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": tflops / peak_tflops, "traffic": traffic_record("k_step<double>"),
+                     "kernel": "k_step<double>",
+                     "peak_source": "measured in this run: 2 x FP64 FMA rate (lbm_probe_fma_rate)",
+                     "flops_per_cell_update": FLOPS_PER_CELL,
+                     "hbm_frac": BYTES_PER_CELL["fp64"] * cells / (ms * 1e-3) / 1e9 / hbm_peak,
+                     "hbm_peak_gbs": hbm_peak,
+                     "bytes_per_cell_update": BYTES_PER_CELL["fp64"]},
+        "status": list(status),
+        "peaks": peaks,
         "e2e": {"value": cells / statistics.mean(e2e_t), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "lbm_set_populations(pinned host) + lbm_step(1) + lbm_moments(pinned host)"},
-        "clocks": dict(clocks.summary(h0, h1), whole_run=clocks.summary()),
+                "path": "lbm_set_populations(pinned host) + lbm_step(1) + lbm_moments(pinned host), "
+                        "FP64, headline grid"},
+        "clocks": dict(clocks.summary(h0 - 0.5, h1 + 0.1),
+                       window="0.5 s before the timed region (the FMA probes and warm-up at "
+                              "full load) to its end",
+                       whole_run=clocks.summary()),
         "gpu_launches": K,
     }
+    if large:
+        line.update(large)
+    line["reflection_600x200"] = refl
+    line["tubes"] = tubes
+    line["von_neumann"] = vn
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         if tubes:
@@ -626,24 +708,31 @@ def run_ours(args):
 
 
 def run_reference(args):
-    """The CPU oracle timed as the reference arm (rank 0 only)."""
+    """The CPU oracle timed as the reference arm (rank 0 only): one process
+    per host core, each stepping one slab of the workload's grid; W warm-up
+    steps, then K timed steps per slab; the job's time is the slowest slab's."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
     w = workload()
-    cells = w.nx * w.ny
-    oracle_steps(steps=args.warmup)
-    n, el = oracle_steps(steps=args.steps)
-    value = cells * n / el
+    cores = os.cpu_count() or 1
+    res = _run_slabs(cores, steps=args.steps, warmup=args.warmup)
+    cells = sum(c for c, _, _ in res)
+    el = max(e for _, _, e in res)
+    value = cells * args.steps / el
+    sample = ("%d host processes, one per core, each stepping one %d-row slab of the %dx%d grid "
+              "as a grid of its own (FP64 numpy oracle): %d warm-up + %d timed steps per slab"
+              % (cores, w.ny // cores, w.nx, w.ny, args.warmup, args.steps))
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n,
-        "warmup": args.warmup, "ms_per_step": el / n * 1e3, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_json(w), "impl": "reference",
-        "path": {"precision": "fp64", "audit_every": 0, "kernel": "numpy oracle, one host thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d full-grid steps of the FP64 numpy oracle, 1 thread" % n},
+        "path": {"precision": "fp64", "audit_every": 0,
+                 "kernel": "numpy oracle, %d host processes" % cores},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -652,21 +741,25 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--audit-every", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-tubes", action="store_true")
     ap.add_argument("--no-vn", action="store_true")
     ap.add_argument("--tube-steps", type=int, default=200)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--cpu-sample", type=int, nargs=2, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sample-tubes", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_sample is not None:
-        print(json.dumps(oracle_steps(seconds=args.cpu_sample)))
+        k, nslabs = args.cpu_sample
+        secs = None if "--steps" in sys.argv else args.cpu_seconds
+        steps = args.steps if "--steps" in sys.argv else None
+        print(json.dumps(oracle_steps(k, nslabs, seconds=secs, steps=steps, warmup=args.warmup)))
         return
     if args.cpu_sample_tubes is not None:
         print(json.dumps(oracle_tube_steps(args.cpu_sample_tubes)))

@@ -241,8 +241,12 @@ const char* lbm_last_error(lbm_ctx* ctx);
  * lbm_audit_noalloc_last_error(). Asynchronous. All calls share the scratch:
  * calls whose kernels overlap on the GPU (different streams or host threads)
  * race and give wrong totals, so issue them one after another in one stream.
- * The first call on a device looks up the scratch's device address; make it
- * before any stream capture that includes this entry point. */
+ * The first call on a device looks up the scratch's device address (with that
+ * device current) and keeps it for the life of the process; make that call
+ * before any stream capture that includes this entry point. A reset of the
+ * device (cudaDeviceReset, or an embedder that tears down and rebuilds the
+ * device's primary context) invalidates the kept address: do not call this
+ * entry point on a device after resetting it. */
 #define LBM_NOALLOC_MAX_BLOCKS 4096
 int lbm_audit_noalloc(const void* f, int precision, int nx, int ny, long long pitch,
                       double dx, double dy, double* totals, void* cuda_stream);

@@ -15,6 +15,7 @@
 // master weights.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only; ranges cost nothing without a profiler attached
 
 #include <cmath>
 #include <cstring>
@@ -618,6 +619,8 @@ int lbm_cnn_set_adam(lbm_cnn* n, double lr, double beta1, double beta2, double e
 int lbm_cnn_loss_grad(lbm_cnn* n, const double* coarse, const double* target, double* loss,
                       float* grads) {
   if (!n || !coarse || !target) return cfail(n, LBM_ERR_INVALID, "NULL argument");
+  nvtxRangePushA("lbm_cnn_train_step");
+  struct Pop { ~Pop() { nvtxRangePop(); } } pop;
   int rc = forward(n, coarse);
   if (rc == LBM_OK) rc = loss_backward(n, target);
   if (rc != LBM_OK) return rc;

@@ -23,6 +23,7 @@
 #include "lbm_step_kernels.cuh"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only; ranges cost nothing without a profiler attached
 
 #include <climits>
 #include <cstddef>
@@ -643,9 +644,22 @@ int lbm_set_init(lbm_ctx* c, const double* rho, const double* u, const double* v
   return rc;
 }
 
+namespace {
+// Profiler range around one lbm_step call ("lbm_step n=<steps>").
+struct StepRange {
+  explicit StepRange(long long n) {
+    char name[48];
+    snprintf(name, sizeof(name), "lbm_step n=%lld", n);
+    nvtxRangePushA(name);
+  }
+  ~StepRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 int lbm_step(lbm_ctx* c, long long nsteps) {
   if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
   if (nsteps < 0) return fail(c, LBM_ERR_INVALID, "nsteps < 0");
+  const StepRange range(nsteps);
   if (c->fuse == 2 && c->cfg.audit_every != 1) {
     while (nsteps >= GRAPH_CHUNK) {
       int rc = ensure_graph2(c, c->cur);

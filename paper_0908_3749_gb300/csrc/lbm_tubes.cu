@@ -24,6 +24,7 @@
 // time. Co-residency is guaranteed by a cooperative launch sized from the
 // occupancy calculator.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only; ranges cost nothing without a profiler attached
 
 #include <algorithm>
 #include <cmath>
@@ -675,6 +676,10 @@ int lbm_batch_step(lbm_batch* b, long long nsteps) {
     b->skip_step = -1;
     return rc;
   }
+  char range[64];
+  snprintf(range, sizeof(range), "lbm_batch_step n=%lld (graph)", nsteps);
+  nvtxRangePushA(range);
+  struct Pop { ~Pop() { nvtxRangePop(); } } pop;
   auto key = std::make_pair(nsteps, b->variant);
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {

@@ -293,7 +293,24 @@ _SIGS.update({
     "lbm_audit_noalloc_last_error": (ctypes.c_char_p, []),
     "lbm_set_fused_steps": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_fused_steps": (ctypes.c_int, [_vp]),
+    "lbm_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_double), _vp]),
 })
+
+PROBE_KINDS = {"fp64": 0, "fp32": 1, "fp32x2": 2}
+
+
+def lbm_probe_fma_rate(kind, millis=50.0, stream=None):
+    """Measured fused multiply-add rate of the current device (lane
+    operations per second) for ``kind`` in PROBE_KINDS."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = ctypes.c_double()
+    rc = load().lbm_probe_fma_rate(PROBE_KINDS[kind], float(millis), ctypes.byref(out),
+                                   _vp(stream or None))
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_probe_fma_rate failed")
+    return out.value
 
 
 def lbm_set_fused_steps(ctx, steps_per_launch):
@@ -308,10 +325,34 @@ NOALLOC_MAX_BLOCKS = 4096
 
 def lbm_audit_noalloc(f, precision, nx, ny, pitch, dx, dy, totals, stream=None):
     """Allocation-free conservation totals of a caller-owned device
-    population tensor into a caller-owned device tensor of 4 doubles."""
+    population tensor into a caller-owned device tensor of 4 doubles.
+
+    The kernel trusts its pointers, so the tensors are checked here first:
+    ``f`` a contiguous CUDA tensor on the current device whose dtype matches
+    the precision (float64 for "fp64", float32 for "fp32") with at least
+    16 * ny * pitch elements; ``totals`` a contiguous float64 CUDA tensor on
+    the same device with at least 4 elements. A mismatch raises LBMError
+    (LBM_ERR_INVALID) without touching the device."""
+    import torch
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    want = {LBM_FP64: torch.float64, LBM_FP32: torch.float32}.get(prec)
+
+    def bad(msg):
+        raise LBMError(LBM_ERR_INVALID, "lbm_audit_noalloc: " + msg)
+
+    for name, t in (("f", f), ("totals", totals)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            bad("%s must be a contiguous CUDA tensor" % name)
+        if t.device.index != torch.cuda.current_device():
+            bad("%s is not on the current device" % name)
+    if want is not None and f.dtype != want:
+        bad("f has dtype %s, precision %s needs %s" % (f.dtype, precision, want))
+    if int(nx) >= 1 and int(ny) >= 1 and f.numel() < 16 * int(ny) * int(pitch):
+        bad("f holds %d elements, 16 x ny x pitch = %d needed" % (f.numel(), 16 * int(ny) * int(pitch)))
+    if totals.dtype != torch.float64 or totals.numel() < 4:
+        bad("totals must be float64 with at least 4 elements")
     rc = load().lbm_audit_noalloc(_dev(f), prec, int(nx), int(ny), int(pitch), float(dx),
                                   float(dy), _dev(totals), _vp(stream or None))
     if rc != LBM_OK:

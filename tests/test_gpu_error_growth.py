@@ -1,0 +1,64 @@
+"""FP64 error-growth curve: the GPU step against the oracle at several time
+levels of one run, per field (relative L-infinity of harness.field_errors
+and of the populations), printed as a table (run pytest with -s to see it).
+
+Runs: the stable Sod tube of the first workload (200 x 4, dx = 0.005,
+dt = 1e-5, the paper's Sod rates x 0.4) to its last level 10 000, and the
+600 x 200 regular shock reflection (Sec. V.B.a geometry) to level 1000.
+Both sides start from the same initial populations and are compared at
+levels 1, 10, 100, 1000 (and 10 000 for the tube). The bar is 1e-12 at
+every level up to 100 and harness.fp64_tol beyond (the oracle's own FP64
+rounding drift, about 1e-14 per step against an extended-precision run).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from harness import field_errors, fp64_tol
+
+pytestmark = pytest.mark.gpu
+
+
+def _curve(w, levels, precision="fp64"):
+    from oracle import scheme
+    from paper_0908_3749_gb300 import lbm
+    cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, precision, 0)
+    ctx = lbm.lbm_create(cfg)
+    rows = []
+    try:
+        lbm.lbm_set_init(ctx, *[np.ascontiguousarray(a) for a in w.fields()])
+        f = scheme.init_populations(*w.fields())
+        ocfg = w.cfg()
+        n = 0
+        for level in levels:
+            f, bad = scheme.run(f, ocfg, level - n, level0=n)
+            lbm.lbm_step(ctx, level - n)
+            n = level
+            got = {k: np.empty((w.ny, w.nx)) for k in ("rho", "u", "v", "T")}
+            lbm.lbm_moments(ctx, got["rho"], got["u"], got["v"], got["T"])
+            rho, u, v, T = scheme.macroscopic(f)
+            err = field_errors(got, {"rho": rho, "u": u, "v": v, "T": T})
+            rows.append((level, err))
+        assert lbm.lbm_status(ctx)[0] == lbm.LBM_OK
+    finally:
+        lbm.lbm_destroy(ctx)
+    print("\n%s (%s): level  rho  u  v  T" % (w.name, precision))
+    for level, err in rows:
+        print("  %6d  %.2e  %.2e  %.2e  %.2e" % (level, err["rho"], err["u"], err["v"], err["T"]))
+    return rows
+
+
+def _assert_bar(rows, name):
+    for level, err in rows:
+        bar = 1e-12 if level <= 100 else fp64_tol(level)
+        assert max(err.values()) <= bar, (name, level, err, bar)
+
+
+def test_error_growth_sod_stable_to_10000():
+    w = W.sod_config1("stable", ny=4)
+    _assert_bar(_curve(w, [1, 10, 100, 1000, 10000]), w.name)
+
+
+def test_error_growth_regular_reflection_to_1000():
+    w = W.regular_reflection()
+    _assert_bar(_curve(w, [1, 10, 100, 1000]), w.name)
