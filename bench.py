@@ -21,14 +21,17 @@ the FP64 fused multiply-add rate measured in this run
 (include/lbm_probe.h), with the HBM fraction beside it.
 
 Lines printed (rank 0): one JSON object. Besides the contract keys:
-``fp32_large_grid``, ``tensor_core_tf32x3`` and
-``fp32_two_steps_per_launch`` are the reduced-precision steps on the same
-grid (64-step CUDA-graph replays back to back) with their errors against an
-FP64 GPU run; ``reflection_600x200`` the 600 x 200 regular shock reflection
+``df64_large_grid`` is the double-word step (FP32 pairs, ~48-bit
+arithmetic on the FP32 units), ``fp32_large_grid``, ``tensor_core_tf32x3``
+and ``fp32_two_steps_per_launch`` the FP32 steps, all on the same grid
+(64-step CUDA-graph replays back to back) with their errors against an FP64
+GPU run; ``reflection_600x200`` the 600 x 200 regular shock reflection
 (Sec. V.B.a geometry) in FP64 and FP32, each step timed alone with the L2
 flushed before it, and as a long run (graph replays, L2-resident);
 ``tubes`` the batch of 4096 quasi-1D Riemann problems (stable and unstable
 tubes counted apart); ``von_neumann`` a stability map of Sec. IV's example;
+``corrector`` the wall time of the learned coarse-grid corrector's use
+against the fine run it stands in for;
 ``peaks`` the measured FMA rates; ``cpu_baseline`` the FP64 numpy oracle on
 the host cores (all cores, and one) over a bounded sample of the headline
 workload; ``e2e`` the headline step through the C ABI with host buffers;
@@ -372,7 +375,8 @@ def large_grid_measure(torch, lbm, stream, audit_every, hbm_peak):
     ref = [np.empty((wl.ny, wl.nx)) for _ in range(4)]
     lbm.lbm_moments(c64, *ref)
     lbm.lbm_destroy(c64)
-    for prec, key, fused in (("fp32", "fp32_large_grid", False),
+    for prec, key, fused in (("df64", "df64_large_grid", False),
+                             ("fp32", "fp32_large_grid", False),
                              ("tc_tf32x3", "tensor_core_tf32x3", False),
                              ("fp32", "fp32_two_steps_per_launch", True)):
         ctx = make_ctx(lbm, wl, prec, 0, stream, tune=not fused)
@@ -392,12 +396,17 @@ def large_grid_measure(torch, lbm, stream, audit_every, hbm_peak):
                 lbm.lbm_destroy(ctx2)
         finally:
             lbm.lbm_destroy(ctx)
-        gbs = BYTES_PER_CELL["fp32"] * cl / (ms * 1e-3) / 1e9
+        gbs = BYTES_PER_CELL["fp64" if prec == "df64" else "fp32"] * cl / (ms * 1e-3) / 1e9
         out[key] = {"workload": "shock_bubble_%dx%d" % (wl.nx, wl.ny), "value": cl / (ms * 1e-3),
                     "unit": UNIT, "ms_per_step": ms, "achieved_gbs": gbs,
                     "frac_of_hbm": gbs / hbm_peak, "step_blocks": blocks,
                     "timing": "64-step CUDA-graph replays back to back (inputs larger than L2)",
                     "error_vs_fp64_gpu_after_%d_steps" % nsteps: err, "status": list(st)}
+        if prec == "df64":
+            out[key]["dtype"] = "f32 double-word (h + l)"
+            out[key]["fp64_equivalent_tflops"] = FLOPS_PER_CELL * cl / (ms * 1e-3) / 1e12
+            out[key]["note"] = ("populations as FP32 pairs (8 B), every step operation in "
+                                "double-word arithmetic on the FP32 units; 256 B per node-update")
         if fused:
             out[key]["note"] = ("two time steps per launch (temporal blocking): the populations "
                                 "cross HBM once per two steps, so achieved_gbs counts the "
@@ -583,12 +592,56 @@ def vn_measure(torch, lbm, stream):
             "launches_per_sweep": 2, "dtype": "f64"}
 
 
+def corrector_measure(torch):
+    """Wall time of the learned coarse-grid corrector's use against the fine
+    run it stands in for (configuration of the learned part: 512 x 512
+    coarse, 4x finer reference, t_end 0.02, FP32 steps): one held-out
+    quadrant problem run fine (2048 x 2048, dt / 4) and coarse, plus one
+    network inference (lbm_cnn_correct). The inference time does not depend
+    on the weights, so an untrained network (identity output) is timed; the
+    trained network's accuracy gain is the GPU test
+    test_gpu_corrector.test_training_gains_at_full_scale."""
+    import workloads
+    from paper_0908_3749_gb300 import corrector, lbm
+    n, r, t_end, dt = 512, 4, 0.02, 1e-5
+    nc = int(round(t_end / dt))
+    wf = workloads.corrector_quadrant(10001, n * r, dt / r)
+    wc = workloads.corrector_quadrant(10001, n, dt)
+    corrector.run_fields(wc, 10)                      # warm-up (library, graphs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, ok_f = corrector.run_fields(wf, nc * r)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    coarse, ok_c = corrector.run_fields(wc, nc)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    net = lbm.lbm_cnn_create(n, n)
+    try:
+        lbm.lbm_cnn_set_params(net, corrector.init_params(0))
+        out = torch.empty_like(coarse)
+        lbm.lbm_cnn_correct(net, coarse, out)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        for _ in range(5):
+            lbm.lbm_cnn_correct(net, coarse, out)
+        torch.cuda.synchronize()
+        t4 = time.perf_counter()
+    finally:
+        lbm.lbm_cnn_destroy(net)
+    inf = (t4 - t3) / 5
+    return {"workload": "2D Riemann quadrant (seed 10001), coarse %dx%d / fine %dx%d, t_end %g, FP32"
+                        % (n, n, n * r, n * r, t_end),
+            "fine_run_s": t1 - t0, "coarse_run_s": t2 - t1, "inference_s": inf,
+            "speedup_vs_fine": (t1 - t0) / (t2 - t1 + inf), "runs_physical": bool(ok_f and ok_c)}
+
+
 def measure_peaks(lbm, stream):
     """FMA rates of this device (lane operations per second), measured now."""
     return {"fp64_fma_per_s": lbm.lbm_probe_fma_rate("fp64", 50.0, stream),
             "fp32_fma_per_s": lbm.lbm_probe_fma_rate("fp32", 50.0, stream),
             "fp32x2_fma_per_s": lbm.lbm_probe_fma_rate("fp32x2", 50.0, stream),
-            "how": "independent FMA chains (8 per thread, 4 x 256 threads per SM), best of 3 "
+            "how": "independent FMA chains (8 per thread, 8 x 256 threads per SM), best of 3 "
                    "launches of ~50 ms (include/lbm_probe.h)"}
 
 
@@ -647,6 +700,7 @@ def run_ours(args):
                                                          hbm_peak, max(K, 20), W)
     tubes = None if args.no_tubes else tubes_measure(torch, lbm, stream, args, hbm_peak)
     vn = None if args.no_vn else vn_measure(torch, lbm, stream)
+    corr = None if args.no_corrector else corrector_measure(torch)
     clocks.stop()
 
     if rank != 0:
@@ -695,9 +749,15 @@ def run_ours(args):
     }
     if large:
         line.update(large)
+        d = large.get("df64_large_grid")
+        if d:
+            d["speedup_vs_fp64_headline"] = ms / d["ms_per_step"]
+            d["fp64_equivalent_frac_of_fp64_peak"] = d["fp64_equivalent_tflops"] / peak_tflops
+            d["fp32_fma_per_s_peak"] = peaks["fp32_fma_per_s"]
     line["reflection_600x200"] = refl
     line["tubes"] = tubes
     line["von_neumann"] = vn
+    line["corrector"] = corr
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         if tubes:
@@ -750,6 +810,7 @@ def main():
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-tubes", action="store_true")
     ap.add_argument("--no-vn", action="store_true")
+    ap.add_argument("--no-corrector", action="store_true")
     ap.add_argument("--tube-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--cpu-sample", type=int, nargs=2, default=None, help=argparse.SUPPRESS)

@@ -54,12 +54,28 @@ enum lbm_precision {
                         the conservation audits */
   LBM_TC_BF16X3 = 2, /* FP32 populations, 16x16 transforms as split-BF16
                         tensor-core products (reserved: LBM_ERR_UNSUPPORTED) */
-  LBM_TC_TF32X3 = 3  /* FP32 populations; m = M f and the back-map M^-1 as
+  LBM_TC_TF32X3 = 3, /* FP32 populations; m = M f and the back-map M^-1 as
                         3xTF32 tensor-core products (tcgen05, FP32
                         accumulation) over 128-node tiles; equilibria,
                         Lax-Wendroff update, moments and audits as LBM_FP32.
                         Grids with 16 x pitch x ny >= 2^32 elements are
                         LBM_ERR_UNSUPPORTED. */
+  LBM_DF64 = 4,      /* double-word: each population stored as the
+                        unevaluated sum h + l of two FP32 numbers (8 bytes,
+                        about 48 significant bits) and every operation of
+                        the step done on the FP32 units with error-free
+                        transformations (TwoSum, FMA-based TwoProd), two nodes
+                        per thread in paired f32x2 instructions; rounding
+                        error per operation of order 2^-48 of its operands
+                        against FP64's 2^-53. Moments and audits in FP64. */
+  LBM_FP32_DWMOM = 5 /* LBM_FP32 populations and transforms, with the
+                        conserved moments (rho, j_x, j_y, e) formed from the
+                        FP32 populations in double-word arithmetic (error-free
+                        butterflies), and the Eq. 14 equilibria and the
+                        temperature recovery P = e - |j|^2 / (2 rho) taken in
+                        double-word from those, rounded to FP32 where they
+                        enter the relaxation; the fused audits sum the
+                        double-word moments. */
 };
 
 /* Boundary kinds (Sec. V). The ghost node outside a side holds
@@ -172,7 +188,8 @@ int lbm_status(lbm_ctx* ctx, long long* first_bad_step, long long* first_negT_st
 long long lbm_step_count(lbm_ctx* ctx);
 
 /* Checkpoint: copies the populations out ([16][ny][nx], x fastest, in the
- * storage precision: double for LBM_FP64, float otherwise) and the step
+ * storage precision: double for LBM_FP64; for LBM_DF64 a pair of floats
+ * (h, l) per population, value h + l; float otherwise) and the step
  * counter. lbm_set_populations restores both; a restored run continues
  * bitwise identically (the step has no atomics or races). */
 int lbm_get_populations(lbm_ctx* ctx, void* f, long long* step, int on_device);
@@ -181,8 +198,9 @@ int lbm_set_populations(lbm_ctx* ctx, const void* f, long long step, int on_devi
 /* Bytes per population element (8 or 4) of ctx. */
 int lbm_element_size(lbm_ctx* ctx);
 
-/* Launch shape of the step (LBM_FP64 / LBM_FP32). The grid is cut into node
- * tiles (32 x 8 nodes in FP32, 32 x 2 in FP64). With one block per tile each
+/* Launch shape of the step (LBM_FP64 / LBM_FP32 / LBM_DF64 / LBM_FP32_DWMOM).
+ * The grid is cut into node tiles (32 x 8 nodes in FP32, 32 x 2 in FP64,
+ * 32 x 4 in LBM_DF64). With one block per tile each
  * block updates its tile; with fewer blocks each block takes tiles b, b + G,
  * b + 2G, ... (G blocks), copying its next tile into shared memory while it
  * computes the current one. Results do not depend on it (each node's update

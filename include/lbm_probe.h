@@ -24,7 +24,7 @@ enum lbm_probe_kind {
 };
 
 /* Times a kernel of independent fused multiply-add chains (8 per thread, 8
- * warps per block, 4 blocks per multiprocessor, every multiprocessor busy)
+ * warps per block, 8 blocks per multiprocessor, every multiprocessor busy)
  * for `kind`, three launches of about `millis` ms each after one warm-up
  * launch, and writes the best rate in lane operations per second (one FMA of
  * one lane = 1; a paired f32x2 instruction counts 2) to *fma_per_s. Work is

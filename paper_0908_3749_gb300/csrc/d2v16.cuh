@@ -312,11 +312,10 @@ __device__ __forceinline__ Cons<R> conserved(const Coeffs<KT>& K, const Groups<R
 }
 
 // Collision of Eq. 3 at one node: df = M^-1 (-dt S_hat (m - m^eq)), given the
-// group values and the conserved moments of the node. Returns P = rho T too.
+// group values and the equilibria q of the node. Returns P = rho T.
 template <typename KT, typename R>
-__device__ __forceinline__ R collide(const Coeffs<KT>& K, const Groups<R>& d,
-                                     const Cons<R>& c, R df[16]) {
-  const Eq<R> q = equilibria(c.rho, c.jx, c.jy, c.e);
+__device__ __forceinline__ R collide_q(const Coeffs<KT>& K, const Groups<R>& d, const Eq<R>& q,
+                                       R df[16]) {
   const R d11 = row4(K.F0, 2, d.S) - q.m11;
   const R d12 = row4(K.F0, 3, d.S);                // m12^eq = 0
   const R d7 = row4(K.FX, 1, d.X) - q.m7;
@@ -342,6 +341,13 @@ __device__ __forceinline__ R collide(const Coeffs<KT>& K, const Groups<R>& d,
   C[3] = K.KS[1][0] * d6 + K.KS[1][1] * d14;
   inverse_transform(S, C, X, Y, df);
   return q.P;
+}
+
+// The same, with the equilibria from the node's conserved moments c.
+template <typename KT, typename R>
+__device__ __forceinline__ R collide(const Coeffs<KT>& K, const Groups<R>& d,
+                                     const Cons<R>& c, R df[16]) {
+  return collide_q(K, d, equilibria(c.rho, c.jx, c.jy, c.e), df);
 }
 
 #endif  // __CUDACC__

@@ -32,6 +32,7 @@
 #include <cstring>
 #include <algorithm>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 using namespace lbmk;
@@ -124,8 +125,10 @@ __global__ void __launch_bounds__(AUX_N) k_audit(const R* __restrict__ f, int nx
   }
 }
 
+// Dirichlet ghost populations; g3 (LBM_DF64, else NULL) gets the third word
+// of each one's double-word split.
 template <typename R>
-__global__ void k_ghost_eq(R* g, const Coeffs<double> K, const double* states) {
+__global__ void k_ghost_eq(R* g, const Coeffs<double> K, const double* states, float* g3) {
   const int side = threadIdx.x;
   if (side >= 4) return;
   const double r = states[4 * side], u = states[4 * side + 1],
@@ -133,7 +136,10 @@ __global__ void k_ghost_eq(R* g, const Coeffs<double> K, const double* states) {
   double out[16];
   feq(K, r, r * u, r * v, r * T + 0.5 * r * (u * u + v * v), out);
 #pragma unroll
-  for (int i = 0; i < 16; ++i) g[16 * side + i] = (R)out[i];
+  for (int i = 0; i < 16; ++i) {
+    g[16 * side + i] = (R)out[i];
+    if (g3) g3[16 * side + i] = third_word(out[i]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -217,6 +223,8 @@ struct lbm_ctx {
   Coeffs<double> Kd;
   CUtensorMap tmap[2];        // TMA descriptors of the two population buffers
   bool tc = false;            // tensor-core transforms (LBM_TC_TF32X3)
+  bool dwp = false;           // double-word populations and arithmetic (LBM_DF64)
+  bool dwmom = false;         // FP32 step, double-word moments (LBM_FP32_DWMOM)
   unsigned char* tc_b = nullptr;  // TF32 parts of M and M^-1 (4 KB)
   float* tc_w = nullptr;          // -dt s_k, 0 for the conserved k
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -244,10 +252,21 @@ int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
 
+// Third words of the double-word split of every constant (LBM_DF64).
+Coeffs<float> third_words(const Coeffs<double>& K) {
+  Coeffs<float> o;
+  const double* s = reinterpret_cast<const double*>(&K);
+  float* d = reinterpret_cast<float*>(&o);
+  for (size_t k = 0; k < sizeof(Coeffs<double>) / sizeof(double); ++k) d[k] = third_word(s[k]);
+  return o;
+}
+
 template <typename R>
 StepArgs<R> make_args(lbm_ctx* c, int slot) {
   StepArgs<R> A;
   A.K = cast_coeffs<R>(c->Kd);
+  if (std::is_same<R, dw>::value) A.K3 = third_words(c->Kd);
+  else memset(&A.K3, 0, sizeof(A.K3));
   A.nx = c->cfg.nx;
   A.ny = c->cfg.ny;
   A.pitch = c->pitch;
@@ -266,6 +285,7 @@ StepArgs<R> make_args(lbm_ctx* c, int slot) {
     A.wall[s][2] = (R)c->cfg.bc[s].T;
   }
   A.geq = (const R*)c->geq;
+  A.geq3 = c->dwp ? (const float*)((const dw*)c->geq + 64) : nullptr;
   A.st = c->st;
   A.partial = c->partial;
   A.audit_every = c->cfg.audit_every;
@@ -277,18 +297,18 @@ StepArgs<R> make_args(lbm_ctx* c, int slot) {
   return A;
 }
 
-template <typename R>
+template <typename R, int VAR = 0>
 int launch_persistent(lbm_ctx* c, cudaStream_t s, int from, void* fout, const StepArgs<R>& A) {
   const dim3 blk(Shape<R>::X, Shape<R>::TY);
   const R* fi = (const R*)c->f[from];
   const CUtensorMap& tm = c->tmap[from];
   if (A.nblocks >= A.ntiles) {
-    if (c->wide) k_step<R, long long><<<A.ntiles, blk, 0, s>>>(tm, fi, (R*)fout, A);
-    else k_step<R, unsigned><<<A.ntiles, blk, 0, s>>>(tm, fi, (R*)fout, A);
+    if (c->wide) k_step<R, long long, VAR><<<A.ntiles, blk, 0, s>>>(tm, fi, (R*)fout, A);
+    else k_step<R, unsigned, VAR><<<A.ntiles, blk, 0, s>>>(tm, fi, (R*)fout, A);
   } else {
     const size_t smem = pipe_smem_bytes<R>();
-    if (c->wide) k_step_pipe<R, long long><<<A.nblocks, blk, smem, s>>>(tm, fi, (R*)fout, A);
-    else k_step_pipe<R, unsigned><<<A.nblocks, blk, smem, s>>>(tm, fi, (R*)fout, A);
+    if (c->wide) k_step_pipe<R, long long, VAR><<<A.nblocks, blk, smem, s>>>(tm, fi, (R*)fout, A);
+    else k_step_pipe<R, unsigned, VAR><<<A.nblocks, blk, smem, s>>>(tm, fi, (R*)fout, A);
   }
   CK(c, cudaGetLastError());
   return LBM_OK;
@@ -301,6 +321,8 @@ int launch_step(lbm_ctx* c, cudaStream_t s, int from) {
                     make_args<float>(c, from), c->tc_b, c->tc_w, c->grid, s));
     return LBM_OK;
   }
+  if (c->dwp) return launch_persistent<dw>(c, s, from, c->f[to], make_args<dw>(c, from));
+  if (c->dwmom) return launch_persistent<float, 1>(c, s, from, c->f[to], make_args<float>(c, from));
   if (c->esize == 8) return launch_persistent<double>(c, s, from, c->f[to], make_args<double>(c, from));
   return launch_persistent<float>(c, s, from, c->f[to], make_args<float>(c, from));
 }
@@ -308,13 +330,14 @@ int launch_step(lbm_ctx* c, cudaStream_t s, int from) {
 // Blocks of a step launch when none were chosen: one per tile (k_step).
 int default_blocks(const lbm_ctx* c) { return c->ntiles; }
 
-template <typename R>
+template <typename R, int VAR = 0>
 cudaError_t allow_pipe_smem() {
   const int b = (int)pipe_smem_bytes<R>();
-  cudaError_t e = cudaFuncSetAttribute(k_step_pipe<R, unsigned>,
+  cudaError_t e = cudaFuncSetAttribute(k_step_pipe<R, unsigned, VAR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_step_pipe<R, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    e = cudaFuncSetAttribute(k_step_pipe<R, long long, VAR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   return e;
 }
 
@@ -386,10 +409,11 @@ EncodeTiledFn tensor_map_encoder() {
 int encode_map(lbm_ctx* c, int b, cuuint32_t rows, CUtensorMap* out) {
   EncodeTiledFn enc = tensor_map_encoder();
   if (!enc) return fail(c, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  const bool dbl = c->esize == 8;
+  const bool dbl = c->esize == 8;  // FP64 or double-word (8-byte elements)
   const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->cfg.ny, 16};
   const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->esize, (cuuint64_t)c->plane * c->esize};
-  const cuuint32_t box[3] = {(cuuint32_t)(dbl ? Tile<double>::BXP : Tile<float>::BXP), rows, 16};
+  const cuuint32_t bxp = c->dwp ? Tile<dw>::BXP : (dbl ? Tile<double>::BXP : Tile<float>::BXP);
+  const cuuint32_t box[3] = {bxp, rows, 16};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = enc(out, dbl ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                          3, c->f[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -403,7 +427,8 @@ int encode_map(lbm_ctx* c, int b, cuuint32_t rows, CUtensorMap* out) {
 int encode_tile_map(lbm_ctx* c, int b) {
   const bool dbl = c->esize == 8;
   const cuuint32_t rows = c->tc ? (cuuint32_t)(TC_Y + 2)
-                                : (cuuint32_t)(dbl ? Tile<double>::ROWS : Tile<float>::ROWS);
+                    : (cuuint32_t)(c->dwp ? Tile<dw>::ROWS
+                                          : (dbl ? Tile<double>::ROWS : Tile<float>::ROWS));
   int rc = encode_map(c, b, rows, &c->tmap[b]);
   if (rc == LBM_OK && !dbl && !c->tc)
     rc = encode_map(c, b, (cuuint32_t)fused_halo_rows(), &c->tmap2[b]);
@@ -487,7 +512,8 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
   if (C.internal_dof != 0)
     return fail(nullptr, LBM_ERR_UNSUPPORTED,
                 "internal_dof != 0: the D2V16 moment set fixes gamma = 2");
-  if (C.precision != LBM_FP64 && C.precision != LBM_FP32 && C.precision != LBM_TC_TF32X3)
+  if (C.precision != LBM_FP64 && C.precision != LBM_FP32 && C.precision != LBM_TC_TF32X3 &&
+      C.precision != LBM_DF64 && C.precision != LBM_FP32_DWMOM)
     return fail(nullptr, LBM_ERR_UNSUPPORTED, "precision not built for the 2D grid path");
   if (C.audit_every < 0) return fail(nullptr, LBM_ERR_INVALID, "audit_every < 0");
   for (int s = 0; s < 4; ++s) {
@@ -516,8 +542,10 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
 
   lbm_ctx* c = new lbm_ctx();
   c->cfg = C;
-  c->esize = C.precision == LBM_FP64 ? 8 : 4;
+  c->esize = (C.precision == LBM_FP64 || C.precision == LBM_DF64) ? 8 : 4;
   c->tc = C.precision == LBM_TC_TF32X3;
+  c->dwp = C.precision == LBM_DF64;
+  c->dwmom = C.precision == LBM_FP32_DWMOM;
   if (!build_coeffs(C, c->Kd)) {
     delete c;
     return fail(nullptr, LBM_ERR_INVALID, "singular moment block");
@@ -531,8 +559,8 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
   }
   c->pitch = ((long long)C.nx + 31) / 32 * 32;
   c->plane = c->pitch * C.ny;
-  const int bx = c->tc ? TC_X : (c->esize == 8 ? Shape<double>::X : Shape<float>::X);
-  const int by = c->tc ? TC_Y : (c->esize == 8 ? Shape<double>::Y : Shape<float>::Y);
+  const int bx = c->tc ? TC_X : (c->dwp ? Shape<dw>::X : (c->esize == 8 ? Shape<double>::X : Shape<float>::X));
+  const int by = c->tc ? TC_Y : (c->dwp ? Shape<dw>::Y : (c->esize == 8 ? Shape<double>::Y : Shape<float>::Y));
   c->tiles_x = (C.nx + bx - 1) / bx;
   c->ntiles = c->tiles_x * ((C.ny + by - 1) / by);
   c->aux_grid = dim3((C.nx + AUX_X - 1) / AUX_X, (C.ny + AUX_Y - 1) / AUX_Y);
@@ -542,19 +570,24 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  if (c->tc) {  // one CTA per tile
-    c->grid = dim3(c->tiles_x, c->ntiles / c->tiles_x);
-    c->nblocks = c->ntiles;
+  if (c->tc) {  // persistent CTAs, each taking every G-th tile
+    c->nblocks = std::max(1, std::min(c->ntiles, TC_CTAS_PER_SM * std::max(1, c->sms)));
+    c->grid = dim3(c->nblocks);
+    if (e == cudaSuccess) e = tc_prepare();
   } else {
     c->nblocks = default_blocks(c);
     c->grid = dim3(c->nblocks);
-    if (e == cudaSuccess) e = c->esize == 8 ? allow_pipe_smem<double>() : allow_pipe_smem<float>();
+    if (e == cudaSuccess)
+      e = c->dwp ? allow_pipe_smem<dw>()
+                 : c->dwmom ? allow_pipe_smem<float, 1>()
+                            : (c->esize == 8 ? allow_pipe_smem<double>() : allow_pipe_smem<float>());
     if (e == cudaSuccess && c->esize == 4) e = fused_prepare();
   }
   const int npartial = std::max(c->ntiles, (int)(c->aux_grid.x * c->aux_grid.y));
   const size_t fbytes = (size_t)16 * c->plane * c->esize;
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&c->f[b], fbytes);
-  if (e == cudaSuccess) e = cudaMalloc(&c->geq, 64 * c->esize);
+  // Dirichlet ghosts: 64 elements (LBM_DF64: then 64 third words)
+  if (e == cudaSuccess) e = cudaMalloc(&c->geq, 64 * c->esize + (c->dwp ? 64 * sizeof(float) : 0));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->st, sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->partial, sizeof(double) * 4 * npartial);
   if (e == cudaSuccess)
@@ -593,10 +626,13 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dstates, states, sizeof(states), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) {
-      if (c->esize == 8)
-        k_ghost_eq<double><<<1, 32, 0, c->stream>>>((double*)c->geq, c->Kd, dstates);
+      if (c->dwp)
+        k_ghost_eq<dw><<<1, 32, 0, c->stream>>>((dw*)c->geq, c->Kd, dstates,
+                                                (float*)((dw*)c->geq + 64));
+      else if (c->esize == 8)
+        k_ghost_eq<double><<<1, 32, 0, c->stream>>>((double*)c->geq, c->Kd, dstates, nullptr);
       else
-        k_ghost_eq<float><<<1, 32, 0, c->stream>>>((float*)c->geq, c->Kd, dstates);
+        k_ghost_eq<float><<<1, 32, 0, c->stream>>>((float*)c->geq, c->Kd, dstates, nullptr);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -632,7 +668,10 @@ int lbm_set_init(lbm_ctx* c, const double* rho, const double* u, const double* v
   }
   const dim3 blk(AUX_X, AUX_Y);
   c->cur = 0;
-  if (c->esize == 8)
+  if (c->dwp)
+    k_init<dw><<<c->aux_grid, blk, 0, c->stream>>>((dw*)c->f[0], p[0], p[1], p[2], p[3], c->Kd,
+                                                c->cfg.nx, c->cfg.ny, c->pitch, c->plane);
+  else if (c->esize == 8)
     k_init<double><<<c->aux_grid, blk, 0, c->stream>>>((double*)c->f[0], p[0], p[1], p[2], p[3],
                                                     c->Kd, c->cfg.nx, c->cfg.ny, c->pitch, c->plane);
   else
@@ -695,7 +734,11 @@ int lbm_moments(lbm_ctx* c, double* rho, double* u, double* v, double* T, int on
   if (!on_device)
     for (int k = 0; k < 4; ++k) d[k] = h[k] ? c->staging + k * n : nullptr;
   const dim3 blk(AUX_X, AUX_Y);
-  if (c->esize == 8)
+  if (c->dwp)
+    k_moments<dw><<<c->aux_grid, blk, 0, c->stream>>>((const dw*)c->f[c->cur], d[0], d[1], d[2],
+                                                   d[3], c->cfg.nx, c->cfg.ny, c->pitch,
+                                                   c->plane, c->Kd);
+  else if (c->esize == 8)
     k_moments<double><<<c->aux_grid, blk, 0, c->stream>>>((const double*)c->f[c->cur], d[0], d[1],
                                                        d[2], d[3], c->cfg.nx, c->cfg.ny,
                                                        c->pitch, c->plane, c->Kd);
@@ -744,7 +787,11 @@ int lbm_audit(lbm_ctx* c, double totals[4]) {
   if (!c || !totals) return fail(c, LBM_ERR_INVALID, "NULL argument");
   const dim3 blk(AUX_X, AUX_Y);
   const double area = c->cfg.dx * c->cfg.dy;
-  if (c->esize == 8)
+  if (c->dwp)
+    k_audit<dw><<<c->aux_grid, blk, 0, c->stream>>>((const dw*)c->f[c->cur], c->cfg.nx, c->cfg.ny,
+                                                 c->pitch, c->plane, area, c->st, c->partial,
+                                                 c->Kd);
+  else if (c->esize == 8)
     k_audit<double><<<c->aux_grid, blk, 0, c->stream>>>((const double*)c->f[c->cur], c->cfg.nx,
                                                      c->cfg.ny, c->pitch, c->plane, area,
                                                      c->st, c->partial, c->Kd);
@@ -878,7 +925,7 @@ int apply_blocks(lbm_ctx* c, int g) {
 // Times `launches` step launches with `g` blocks that read the current buffer
 // and write the spare one, against a scratch status (no audit), so the
 // state, the step counter and the audit log are untouched. Mean ms / launch.
-template <typename R>
+template <typename R, int VAR = 0>
 int time_blocks(lbm_ctx* c, int g, int launches, DevStatus* scratch, cudaEvent_t e0,
                 cudaEvent_t e1, float* ms) {
   CK(c, cudaMemsetAsync(scratch, 0, offsetof(DevStatus, audit_totals), c->stream));
@@ -889,7 +936,7 @@ int time_blocks(lbm_ctx* c, int g, int launches, DevStatus* scratch, cudaEvent_t
   for (int j = 0; j < 2 + launches; ++j) {
     if (j == 2) CK(c, cudaEventRecord(e0, c->stream));
     A.slot = j & 1;
-    const int rc = launch_persistent<R>(c, c->stream, c->cur, c->f[1 - c->cur], A);
+    const int rc = launch_persistent<R, VAR>(c, c->stream, c->cur, c->f[1 - c->cur], A);
     if (rc != LBM_OK) return rc;
   }
   CK(c, cudaEventRecord(e1, c->stream));
@@ -906,7 +953,7 @@ extern "C" {
 int lbm_set_step_blocks(lbm_ctx* c, int blocks) {
   if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
   if (blocks < 0) return fail(c, LBM_ERR_INVALID, "blocks < 0");
-  if (c->tc) return fail(c, LBM_ERR_UNSUPPORTED, "the tensor-core step runs one CTA per tile");
+  if (c->tc) return fail(c, LBM_ERR_UNSUPPORTED, "the tensor-core step sets its own launch");
   return apply_blocks(c, blocks == 0 ? default_blocks(c) : std::min(blocks, c->ntiles));
 }
 
@@ -915,7 +962,7 @@ int lbm_step_blocks(lbm_ctx* c) { return c ? c->nblocks : -1; }
 int lbm_set_fused_steps(lbm_ctx* c, int steps) {
   if (!c) return fail(nullptr, LBM_ERR_INVALID, "ctx is NULL");
   if (steps != 1 && steps != 2) return fail(c, LBM_ERR_INVALID, "steps per launch must be 1 or 2");
-  if (steps == 2 && (c->tc || c->esize != 4))
+  if (steps == 2 && (c->tc || c->dwmom || c->esize != 4))
     return fail(c, LBM_ERR_UNSUPPORTED, "two steps per launch: LBM_FP32 contexts only");
   c->fuse = steps;
   return LBM_OK;
@@ -930,7 +977,8 @@ int lbm_autotune(lbm_ctx* c, int launches) {
   // Candidates: one tile per block (k_step), and for k_step_pipe 1 ..
   // MINB_PIPE blocks per SM and ceil(ntiles / m) blocks for m = 2 .. 8 tiles
   // per block.
-  const int per_sm = c->esize == 8 ? Shape<double>::MINB_PIPE : Shape<float>::MINB_PIPE;
+  const int per_sm = c->dwp ? Shape<dw>::MINB_PIPE
+                            : (c->esize == 8 ? Shape<double>::MINB_PIPE : Shape<float>::MINB_PIPE);
   std::vector<int> cand;
   auto add = [&](long long g) {
     const int v = (int)std::max(1ll, std::min((long long)c->ntiles, g));
@@ -947,8 +995,10 @@ int lbm_autotune(lbm_ctx* c, int launches) {
     rc = fail(c, LBM_ERR_CUDA, "cudaEventCreate failed");
   for (size_t i = 0; i < cand.size() && rc == LBM_OK; ++i) {
     float ms = 0.f;
-    rc = c->esize == 8 ? time_blocks<double>(c, cand[i], launches, scratch, e0, e1, &ms)
-                       : time_blocks<float>(c, cand[i], launches, scratch, e0, e1, &ms);
+    rc = c->dwp ? time_blocks<dw>(c, cand[i], launches, scratch, e0, e1, &ms)
+         : c->dwmom ? time_blocks<float, 1>(c, cand[i], launches, scratch, e0, e1, &ms)
+         : c->esize == 8 ? time_blocks<double>(c, cand[i], launches, scratch, e0, e1, &ms)
+                         : time_blocks<float>(c, cand[i], launches, scratch, e0, e1, &ms);
     if (rc == LBM_OK && (i == 0 || ms < best_ms)) {
       best_ms = ms;
       best = cand[i];

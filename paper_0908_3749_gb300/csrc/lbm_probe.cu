@@ -4,7 +4,7 @@
 // step (FP32 units).
 //
 // Each thread runs 8 independent chains a <- a * b + c, enough independent
-// work per warp to cover the units' latency; every multiprocessor runs 4
+// work per warp to cover the units' latency; every multiprocessor runs 8
 // blocks of 8 warps. The chains' final values are compared with a value they
 // cannot take, so the compiler keeps every operation and nothing is written.
 #include <cuda_runtime.h>
@@ -17,7 +17,7 @@
 
 namespace {
 
-constexpr int PROBE_THREADS = 256, PROBE_BLOCKS_PER_SM = 4, CHAINS = 8;
+constexpr int PROBE_THREADS = 256, PROBE_BLOCKS_PER_SM = 8, CHAINS = 8;
 
 template <int KIND>
 __global__ void __launch_bounds__(PROBE_THREADS) k_fma_probe(long long iters, double* out) {

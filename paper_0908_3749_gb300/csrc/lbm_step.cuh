@@ -10,6 +10,7 @@
 #include "../../include/lbm.h"
 #include "coeffs.h"
 #include "d2v16.cuh"
+#include "dw.cuh"
 #include "tma.cuh"
 
 namespace lbmk {
@@ -41,6 +42,19 @@ template <> struct Shape<float> {
 template <> struct Shape<double> {
   static constexpr int X = 32, Y = 2, TY = 2, MINB = 8, MINB_PIPE = 6;
 };
+// Double-word (LBM_DF64): 32 x 4 tiles of 8-byte elements (below the 48 KB
+// of static shared memory), FP32-ALU-bound. LBM_DW_LANES = 1: one node per
+// thread; 2: two rows per thread in paired f32x2 instructions (half the
+// instructions issued, twice the registers; the FP32 units retire the same
+// lanes per clock either way).
+#ifndef LBM_DW_LANES
+#define LBM_DW_LANES 1
+#endif
+template <> struct Shape<dw> {
+  static constexpr int X = 32, Y = 4, TY = Y / LBM_DW_LANES;
+  static constexpr int MINB = LBM_DW_LANES == 1 ? 5 : 6, MINB_PIPE = LBM_DW_LANES == 1 ? 3 : 3;
+  static_assert(LBM_DW_LANES == 1 || LBM_DW_LANES == 2, "one or two nodes per thread");
+};
 constexpr int AUX_X = 32, AUX_Y = 8, AUX_N = AUX_X * AUX_Y;  // init / moments / audit
 
 // Device-resident status block of one context.
@@ -66,6 +80,7 @@ struct DevStatus {
 template <typename R>
 struct StepArgs {
   Coeffs<R> K;
+  Coeffs<float> K3;   // LBM_DF64: third words of K (K = K.h + K.l + K3); else unused
   int nx, ny;
   long long pitch, plane;
   int bc[4];          // x-, x+, y-, y+
@@ -75,6 +90,7 @@ struct StepArgs {
   R hx, hy, dtr;      // dx, dy, dt (positions along a side, time)
   R wall[4][3];       // (u, v, T) of LBM_BC_WALL sides
   const R* geq;       // [4][16] Dirichlet ghost populations
+  const float* geq3;  // LBM_DF64: their third words; else unused
   DevStatus* st;
   double* partial;    // [ntiles][4] audit scratch: one partial sum per tile
   int audit_every;
@@ -94,6 +110,7 @@ __device__ __forceinline__ double widen(float x) {
   return d;
 }
 __device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(dw x) { return widen(x.h) + widen(x.l); }
 
 // ---------------------------------------------------------------------------
 // Fixed-order FP64 reductions of four sums (bitwise reproducible)
@@ -413,10 +430,33 @@ __device__ __forceinline__ void audit_finish(const StepArgs<R>& A, unsigned long
   }
 }
 
+// Audit partial of a tile whose threads each hold two nodes (rows y and
+// y + BYD/2): two warp passes, then the rows 0 .. BYD-1 in order.
+template <int BXD, int BYD, typename R>
+__device__ __forceinline__ void audit_pair_rows(const StepArgs<R>& A, int cur, const double (&va)[4],
+                                                const double (&vb)[4], double (*sm)[4]) {
+  constexpr int HY = BYD / 2;
+  const int lane = threadIdx.x;
+  const double ka = warp_sum4(va, lane), kb = warp_sum4(vb, lane);
+  if ((lane & 7) == 0) {
+    sm[threadIdx.y][lane >> 3] = ka;
+    sm[threadIdx.y + HY][lane >> 3] = kb;
+  }
+  __syncthreads();
+  const int t = threadIdx.y * BXD + threadIdx.x;
+  if (t < 4) {
+    double s = 0.0;
+    for (int w = 0; w < BYD; ++w) s += sm[w][t];
+    A.partial[4 * cur + t] = s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Tensor-core step (lbm_tc.cu)
 // ---------------------------------------------------------------------------
-constexpr int TC_X = 32, TC_Y = 4;  // nodes per CTA: 32 x 4 = 128
+constexpr int TC_X = 32, TC_Y = 4;  // nodes per tile: 32 x 4 = 128 (one per thread)
+constexpr int TC_CTAS_PER_SM = 4;   // persistent CTAs per SM
+cudaError_t tc_prepare();           // shared-memory attribute of the kernel
 // TF32 high/low parts of M and M^-1 in the layout the kernel stages (4 x 1 KB).
 void tc_prepare_constants(const double (&M)[16][16], const double (&Minv)[16][16],
                           unsigned char (&out)[4][1024]);

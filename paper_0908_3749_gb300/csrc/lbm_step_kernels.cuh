@@ -4,6 +4,9 @@
 // launches them (the only translation unit that includes this header).
 #pragma once
 
+#include <type_traits>
+
+#include "lbm_dw_step.cuh"
 #include "lbm_step.cuh"
 
 namespace lbmk {
@@ -82,7 +85,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<R>& A, const R* __restr
 // finishes node by node through the scalar neighbour_terms (ghosts, periodic
 // wraps). Audit steps: per-tile sums of the Y rows in a fixed order (two warp
 // passes, then rows 0 .. Y-1).
-template <typename Off>
+// MAC (precision LBM_FP32_DWMOM): the conserved moments (rho, j, e) of the
+// FP32 populations, the Eq. 14 equilibria and P = rho T in double-word
+// arithmetic (lbm_dw_step.cuh), rounded to FP32 only where they enter the
+// FP32 relaxation; audits sum the double-word moments.
+template <typename Off, bool MAC = false>
 __device__ __forceinline__ void step_tile_x2(const StepArgs<float>& A, const float* __restrict__ fin,
                                              float* __restrict__ fout, const float* stage, int cur,
                                              bool audit, float t, double (*sm)[4], bool& bad,
@@ -94,6 +101,7 @@ __device__ __forceinline__ void step_tile_x2(const StepArgs<float>& A, const flo
   const int ya = (cur / A.tiles_x) * BYD + threadIdx.y, yb = ya + HY;
   const bool act_a = x < A.nx && ya < A.ny, act_b = x < A.nx && yb < A.ny;  // act_b => act_a
   float mca[4] = {0.f, 0.f, 0.f, 0.f}, mcb[4] = {0.f, 0.f, 0.f, 0.f};
+  dw wca[4], wcb[4];  // MAC: the double-word conserved moments for the audit
   if (act_a) {
     const Off P = (Off)A.plane, pitch = (Off)A.pitch;
     const Off ca = (Off)ya * pitch + (Off)x, cb = ca + (Off)HY * pitch;
@@ -104,9 +112,32 @@ __device__ __forceinline__ void step_tile_x2(const StepArgs<float>& A, const flo
     for (int i = 0; i < 16; ++i) f[i] = F2(sa[i * PS], sb[i * PS]);
     Groups<F2> d;
     transform(f, d);
-    const Cons<F2> m = conserved(A.K, d);
+    Cons<F2> m;
     F2 acc[16];
-    const F2 press = collide(A.K, d, m, acc);
+    F2 press;
+    if constexpr (MAC) {
+      float2 fv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) fv[i] = f[i].v;
+      DW<float2> rho, jx, jy, e;
+      dw_conserved_of(fv, rho, jx, jy, e);
+      rho = dnorm(rho); jx = dnorm(jx); jy = dnorm(jy); e = dnorm(e);
+      const DwEq<float2> qd = dw_equilibria(rho, jx, jy, e);
+      auto r32 = [](DW<float2> v) { return F2(dnorm(v).h); };
+      Eq<F2> q;
+      q.m5 = r32(qd.m5); q.m6 = r32(qd.m6); q.m7 = r32(qd.m7); q.m8 = r32(qd.m8);
+      q.m9 = r32(qd.m9); q.m10 = r32(qd.m10); q.m11 = r32(qd.m11); q.m13 = r32(qd.m13);
+      q.m14 = r32(qd.m14); q.P = r32(qd.P);
+      m.rho = F2(rho.h); m.jx = F2(jx.h); m.jy = F2(jy.h); m.e = F2(e.h);
+      press = collide_q(A.K, d, q, acc);
+      wca[0] = dw(rho.h.x, rho.l.x); wca[1] = dw(jx.h.x, jx.l.x);
+      wca[2] = dw(jy.h.x, jy.l.x); wca[3] = dw(e.h.x, e.l.x);
+      wcb[0] = dw(rho.h.y, rho.l.y); wcb[1] = dw(jx.h.y, jx.l.y);
+      wcb[2] = dw(jy.h.y, jy.l.y); wcb[3] = dw(e.h.y, e.l.y);
+    } else {
+      m = conserved(A.K, d);
+      press = collide(A.K, d, m, acc);
+    }
 #pragma unroll
     for (int i = 0; i < 16; ++i) acc[i] = A.K.a0[i] * f[i] + acc[i];
 
@@ -151,32 +182,33 @@ __device__ __forceinline__ void step_tile_x2(const StepArgs<float>& A, const flo
     }
   }
   if (audit) {  // FP64 only on audit steps
-    const int lane = threadIdx.x;
-    const double va[4] = {widen(mca[0]), widen(mca[1]), widen(mca[2]), widen(mca[3])};
-    const double vb[4] = {widen(mcb[0]), widen(mcb[1]), widen(mcb[2]), widen(mcb[3])};
-    const double ka = warp_sum4(va, lane), kb = warp_sum4(vb, lane);
-    if ((lane & 7) == 0) {
-      sm[threadIdx.y][lane >> 3] = ka;
-      sm[threadIdx.y + HY][lane >> 3] = kb;
+    double va[4], vb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if constexpr (MAC) {
+        va[q] = act_a ? widen(wca[q]) : 0.0;
+        vb[q] = act_b ? widen(wcb[q]) : 0.0;
+      } else {
+        va[q] = widen(mca[q]);
+        vb[q] = widen(mcb[q]);
+      }
     }
-    __syncthreads();
-    const int t = threadIdx.y * BXD + threadIdx.x;
-    if (t < 4) {
-      double s = 0.0;
-      for (int w = 0; w < BYD; ++w) s += sm[w][t];
-      A.partial[4 * cur + t] = s;
-    }
+    audit_pair_rows<BXD, BYD>(A, cur, va, vb, sm);
   }
 }
 
-template <typename R, typename Off>
+// VAR selects a variant of the FP32 step: 0 the plain one, 1 the one with
+// double-word conserved moments and equilibria (LBM_FP32_DWMOM).
+template <typename R, typename Off, int VAR>
 __device__ __forceinline__ void step_any(const StepArgs<R>& A, const R* __restrict__ fin,
                                          R* __restrict__ fout, const R* stage, int cur, bool audit,
                                          R t, double (*sm)[4], bool& bad, bool& negT) {
-  if constexpr (Shape<R>::TY == Shape<R>::Y)
+  if constexpr (std::is_same<R, dw>::value)
+    step_tile_dw<Off>(A, fin, fout, stage, cur, audit, t, sm, bad, negT);
+  else if constexpr (Shape<R>::TY == Shape<R>::Y)
     step_tile<R, Off>(A, fin, fout, stage, cur, audit, t, sm, bad, negT);
   else
-    step_tile_x2<Off>(A, fin, fout, stage, cur, audit, t, sm, bad, negT);
+    step_tile_x2<Off, VAR == 1>(A, fin, fout, stage, cur, audit, t, sm, bad, negT);
 }
 
 // Blocks per SM the one-tile form is compiled for: the FP32 form with 64-bit
@@ -186,7 +218,7 @@ constexpr int step_minb() {
   return (sizeof(R) == 4 && sizeof(Off) == 8) ? Shape<R>::MINB - 1 : Shape<R>::MINB;
 }
 
-template <typename R, typename Off>
+template <typename R, typename Off, int VAR = 0>
 __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, (step_minb<R, Off>()))
     k_step(const __grid_constant__ CUtensorMap tmap, const R* __restrict__ fin,
            R* __restrict__ fout, const StepArgs<R> A) {
@@ -218,7 +250,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, (step_minb<R, Off>
     return;
   }
   bool bad = false, negT = false;
-  step_any<R, Off>(A, fin, fout, tile, blockIdx.x, audit, A.dtr * R(s_step), sm, bad, negT);
+  step_any<R, Off, VAR>(A, fin, fout, tile, blockIdx.x, audit, A.dtr * R(s_step), sm, bad, negT);
   const unsigned long long step = s_step;
   watchdog_flags(A.st, step, bad, negT);
   if (audit) audit_finish<N>(A, step, sm, &s_last);
@@ -231,7 +263,7 @@ constexpr size_t pipe_smem_bytes() { return 2 * sizeof(R) * (size_t)Tile<R>::ELE
 static_assert(sizeof(float) * Tile<float>::ELEMS % 128 == 0, "stage size");
 static_assert(sizeof(double) * Tile<double>::ELEMS % 128 == 0, "stage size");
 
-template <typename R, typename Off>
+template <typename R, typename Off, int VAR = 0>
 __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB_PIPE)
     k_step_pipe(const __grid_constant__ CUtensorMap tmap, const R* __restrict__ fin,
                 R* __restrict__ fout, const StepArgs<R> A) {
@@ -272,7 +304,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB_PIP
       }
       return;
     }
-    step_any<R, Off>(A, fin, fout, stages + s * Tile<R>::ELEMS, cur, s_audit != 0,
+    step_any<R, Off, VAR>(A, fin, fout, stages + s * Tile<R>::ELEMS, cur, s_audit != 0,
                      A.dtr * R(s_step), sm, bad, negT);
     __syncthreads();  // stage s and sm are free again
   }

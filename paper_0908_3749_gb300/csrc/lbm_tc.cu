@@ -2,26 +2,30 @@
 // 5th-generation tensor cores (tcgen05.mma, TMEM accumulators), precision
 // LBM_TC_TF32X3 of include/lbm.h.
 //
-// One CTA = 128 nodes (a 32 x 4 tile) = 128 threads = 4 warps; node t of the
-// tile is row t of the MMA and lane t of tensor memory. Per step:
-//   1. TMA: the tile and its halo (all 16 FP32 populations) into shared
-//      memory, as in the FP32 step.
-//   2. A = f (128 x 16) split into TF32 high and low parts, written to shared
-//      memory in the canonical K-major layout without swizzle (8-row x 16-byte
-//      core matrices).
+// Persistent CTAs of 128 threads (4 warps, TC_CTAS_PER_SM per SM), each taking
+// node tiles b, b + G, b + 2G, ... (G CTAs); a tile is 32 x 4 = 128 nodes,
+// node t of the tile is row t of the MMA and lane t of tensor memory. Once
+// per CTA: 32 TMEM columns are allocated, the transform constants copied to
+// shared memory and the first tile's copy started. Per tile:
+//   0. TMA: the next tile and its halo into the other shared-memory stage
+//      (double buffering: the copy runs under this tile's work);
+//   1. wait for this tile's copy;
+//   2. A = f (128 x 16) split into TF32 high and low parts (round to nearest,
+//      ties away, by integer rounding of the bit pattern), written to shared
+//      memory in the canonical K-major layout without swizzle;
 //   3. m = f M^T: three products A_hi B_hi + A_hi B_lo + A_lo B_hi (the
-//      3xTF32 split, error ~ the FP32 one), each two K = 8 MMAs, issued by one
+//      3xTF32 split, error ~ the FP32 one), each two K = 8 MMAs issued by one
 //      thread into TMEM columns 0..15 (FP32 accumulation); tcgen05.ld gives
-//      every thread the 16 moments of its node.
-//   4. Eq. 14 equilibria and the relaxation of Eq. 3 per node on the CUDA
-//      cores: dm_k = -dt s_k (m_k - m_k^eq).
-//   5. df = dm (M^-1)^T, the same three-product split, into TMEM columns
-//      16..31; tcgen05.ld.
+//      every thread the 16 moments of its node;
+//   4. Eq. 14 equilibria and the relaxation of Eq. 3 on the CUDA cores:
+//      dm_k = -dt s_k (m_k - m_k^eq);
+//   5. df = dm (M^-1)^T, the same split, into TMEM columns 16..31; ld;
 //   6. Lax-Wendroff update with the tile's neighbours, ghosts at the domain
-//      edge, store; watchdog and audit epilogue as in the FP32 step.
-// Every wait (TMA, MMA completion) is bounded in time; on expiry the kernel
-// records LBM_ERR_TIMEOUT, waits once more for its own operations (bounded),
-// frees its tensor memory and returns.
+//      edge, store; audit partial of the tile on audit steps.
+// Watchdog and audit epilogue once per CTA. Every wait (TMA, MMA completion)
+// is bounded in time; on expiry the kernel records LBM_ERR_TIMEOUT, waits
+// once more for the copies and products it issued (bounded), frees its
+// tensor memory and returns.
 #include "lbm_step.cuh"
 
 #include <cstring>
@@ -59,12 +63,6 @@ __device__ __forceinline__ unsigned long long smem_desc(unsigned addr) {
 constexpr unsigned TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) |
                               ((128u >> 4) << 24);
 
-__device__ __forceinline__ float tf32_rn(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
 __device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long a, unsigned long long b,
                                        unsigned accumulate) {
   asm volatile(
@@ -101,23 +99,6 @@ __device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Writes the TF32 high and low parts of v (16 values of row `row`) into the
-// two operand buffers (16-byte stores, one per core-matrix row segment).
-__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int row,
-                                          const float (&v)[16]) {
-#pragma unroll
-  for (int kq = 0; kq < 4; ++kq) {
-    float h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      h[e] = tf32_rn(v[4 * kq + e]);
-      l[e] = tf32_rn(v[4 * kq + e] - h[e]);
-    }
-    *reinterpret_cast<float4*>(hi + canon(row, 4 * kq)) = make_float4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<float4*>(lo + canon(row, 4 * kq)) = make_float4(l[0], l[1], l[2], l[3]);
-  }
-}
-
 // Six MMAs: D = A_hi B_hi + A_hi B_lo + A_lo B_hi over K = 16 (two K = 8 halves).
 __device__ __forceinline__ void tc_product(unsigned tmem_d, unsigned a_hi, unsigned a_lo,
                                            unsigned b_hi, unsigned b_lo) {
@@ -130,29 +111,59 @@ __device__ __forceinline__ void tc_product(unsigned tmem_d, unsigned a_hi, unsig
              (p | h) ? 1u : 0u);
 }
 
+// TF32 rounding of an FP32 value (nearest, ties away from zero: half of the
+// last kept bit added to the magnitude's bit pattern, the 13 low bits
+// cleared): two integer operations instead of a conversion.
+__device__ __forceinline__ float tf32_rna(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// Writes the TF32 high and low parts of v (16 values of row `row`) into the
+// two operand buffers: hi = tf32(v), lo = tf32(v - hi) (v - hi is exact).
+__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int row,
+                                              const float (&v)[16]) {
+#pragma unroll
+  for (int kq = 0; kq < 4; ++kq) {
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      h[e] = tf32_rna(v[4 * kq + e]);
+      l[e] = tf32_rna(__fsub_rn(v[4 * kq + e], h[e]));
+    }
+    *reinterpret_cast<float4*>(hi + canon(row, 4 * kq)) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(lo + canon(row, 4 * kq)) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
+
 struct TcSmem {
-  float tile[TC_TILE];                       // populations + halo (TMA)
+  float tile[2][TC_TILE];                      // two stages: populations + halo (TMA)
   alignas(128) unsigned char a_hi[TC_N * 64];  // 128 x 16 TF32, canonical layout
   alignas(128) unsigned char a_lo[TC_N * 64];
-  alignas(128) unsigned char b[4][16 * 64];  // M hi, M lo, M^-1 hi, M^-1 lo (16 x 16)
-  unsigned long long bar_tma, bar_mma;
+  alignas(128) unsigned char b[4][16 * 64];    // M hi, M lo, M^-1 hi, M^-1 lo (16 x 16)
+  unsigned long long bar_tma[2], bar_mma;
   unsigned tmem_base;
-  int flag;
   double red[TC_N / 4][4];
   unsigned long long step;
   int audit, last;
 };
+static_assert(TC_TILE * sizeof(float) % 128 == 0, "stages stay 128-byte aligned");
 
-__global__ void __launch_bounds__(TC_N, 1)
+__device__ __forceinline__ void tc_load_tile(float* dst, const CUtensorMap* tmap,
+                                             unsigned long long* bar, int tile, int tiles_x) {
+  mbar_expect_tx(bar, TC_TILE_BYTES);
+  tma_load_tile(dst, tmap, (tile % tiles_x) * TC_X - HALO_X, (tile / tiles_x) * TC_Y - 1, bar);
+}
+
+__global__ void __launch_bounds__(TC_N, TC_CTAS_PER_SM)
     k_step_tc(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ fin,
               float* __restrict__ fout, const StepArgs<float> A,
               const unsigned char* __restrict__ bconst, const float* __restrict__ wk) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
-  const int x0 = blockIdx.x * TC_X, y0 = blockIdx.y * TC_Y;
+  const int G = (int)gridDim.x;
 
-  if (warp == 0) {  // tensor memory: 32 columns for this CTA
+  if (warp == 0) {  // tensor memory: 32 columns for this CTA, for all its tiles
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&S.tmem_base)),
                  "r"(TC_TMEM_COLS)
@@ -160,10 +171,10 @@ __global__ void __launch_bounds__(TC_N, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    mbar_init(&S.bar_tma, 1);
+    mbar_init(&S.bar_tma[0], 1);
+    mbar_init(&S.bar_tma[1], 1);
     mbar_init(&S.bar_mma, 1);
-    mbar_expect_tx(&S.bar_tma, TC_TILE_BYTES);
-    tma_load_tile(S.tile, &tmap, x0 - HALO_X, y0 - 1, &S.bar_tma);
+    tc_load_tile(S.tile[0], &tmap, &S.bar_tma[0], blockIdx.x, A.tiles_x);  // grid <= ntiles
     S.step = read_step(A, &S.audit);
   }
   // transform constants into shared memory (4 KB)
@@ -173,83 +184,121 @@ __global__ void __launch_bounds__(TC_N, 1)
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = S.tmem_base;
+  const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
   const unsigned long long step = S.step;
   const bool audit = S.audit != 0;
-  bool ok = __syncthreads_and(mbar_wait_bounded(&S.bar_tma, 0, TMA_WAIT_CYCLES));
-
+  const float tnow = A.dtr * (float)step;
   const int tx = t & 31, ty = t >> 5;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool active = x < A.nx && y < A.ny;
-  const float* ctr = S.tile + (ty + 1) * TC_BXP + tx + HALO_X;
   constexpr int PS = TC_ROWS * TC_BXP;
-  float f[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) f[i] = ctr[i * PS];
+  const unsigned P = (unsigned)A.plane, pitch = (unsigned)A.pitch;
 
-  // m = f M^T on the tensor cores. `issued` counts the MMA batches committed
-  // to bar_mma (the same in every thread: `ok` is block-uniform).
-  int issued = 0;
-  if (ok) {
+  bool bad = false, negT = false;
+  unsigned mma_done = 0;  // MMA batches committed to bar_mma and waited for
+  // Failure state: which waits gave up (-1: none) and what is still in flight.
+  int failed = 0, wait_tma = -1, wait_next = -1, wait_mma = 0;
+  int k = 0;
+  for (int cur = blockIdx.x; cur < A.ntiles; cur += G, ++k) {
+    const int s = k & 1;
+    const bool more = cur + G < A.ntiles;
+    // Stage 1 - s was released at the end of the previous tile.
+    if (t == 0 && more) tc_load_tile(S.tile[1 - s], &tmap, &S.bar_tma[1 - s], cur + G, A.tiles_x);
+    if (!__syncthreads_and(mbar_wait_bounded(&S.bar_tma[s], (k >> 1) & 1, TMA_WAIT_CYCLES))) {
+      failed = 1;
+      wait_tma = s * 2 + ((k >> 1) & 1);
+      if (more) wait_next = (1 - s) * 2 + (((k + 1) >> 1) & 1);
+      break;
+    }
+    const int x = (cur % A.tiles_x) * TC_X + tx, y = (cur / A.tiles_x) * TC_Y + ty;
+    const bool active = x < A.nx && y < A.ny;
+    const float* ctr = S.tile[s] + (ty + 1) * TC_BXP + tx + HALO_X;
+    float f[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) f[i] = ctr[i * PS];
+
+    // m = f M^T on the tensor cores
     put_split(S.a_hi, S.a_lo, t, f);
     fence_async_smem();
-  }
-  __syncthreads();
-  if (ok && t == 0) {
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      tc_product(tmem, smem_addr(S.a_hi), smem_addr(S.a_lo), smem_addr(S.b[0]), smem_addr(S.b[1]));
+      tc_commit(&S.bar_mma);
+    }
+    if (!__syncthreads_and(mbar_wait_bounded(&S.bar_mma, mma_done & 1, TMA_WAIT_CYCLES))) {
+      failed = 1;
+      wait_mma = 1;
+      if (more) wait_next = (1 - s) * 2 + (((k + 1) >> 1) & 1);
+      break;
+    }
+    ++mma_done;
     tc_fence_after();
-    tc_product(tmem, smem_addr(S.a_hi), smem_addr(S.a_lo), smem_addr(S.b[0]), smem_addr(S.b[1]));
-    tc_commit(&S.bar_mma);
-  }
-  if (ok) {
-    issued = 1;
-    ok = __syncthreads_and(mbar_wait_bounded(&S.bar_mma, 0, TMA_WAIT_CYCLES));
-  }
-  float m[16];
-  if (ok) {
-    tc_fence_after();
-    tc_ld16(tmem + ((unsigned)(warp * 32) << 16), m);
-  }
+    float m[16];
+    tc_ld16(trow, m);
 
-  // equilibria and relaxation on the CUDA cores
-  Cons<float> c;
-  c.rho = m[0]; c.jx = m[1]; c.jy = m[2]; c.e = m[3];
-  float press = 0.f;
-  if (ok) {
+    // equilibria and relaxation on the CUDA cores
+    Cons<float> c;
+    c.rho = m[0]; c.jx = m[1]; c.jy = m[2]; c.e = m[3];
     const Eq<float> q = equilibria(c.rho, c.jx, c.jy, c.e);
-    press = q.P;
-    const float meq[16] = {m[0], m[1], m[2], m[3], q.m5, q.m6, q.m7, q.m8, q.m9, q.m10,
-                           q.m11, 0.f, q.m13, q.m14, 0.f, 0.f};
-    float dm[16];
+    {
+      const float meq[16] = {m[0], m[1], m[2], m[3], q.m5, q.m6, q.m7, q.m8, q.m9, q.m10,
+                             q.m11, 0.f, q.m13, q.m14, 0.f, 0.f};
+      float dm[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) dm[k] = wk[k] * (m[k] - meq[k]);
-    tc_fence_before();   // the tcgen05.ld above completes before A is rewritten
-    put_split(S.a_hi, S.a_lo, t, dm);
-    fence_async_smem();
-  }
-  __syncthreads();
-  if (ok && t == 0) {
+      for (int kk = 0; kk < 16; ++kk) dm[kk] = wk[kk] * (m[kk] - meq[kk]);
+      tc_fence_before();  // the tcgen05.ld above completes before A is rewritten
+      put_split(S.a_hi, S.a_lo, t, dm);
+      fence_async_smem();
+    }
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      tc_product(tmem + 16, smem_addr(S.a_hi), smem_addr(S.a_lo), smem_addr(S.b[2]),
+                 smem_addr(S.b[3]));
+      tc_commit(&S.bar_mma);
+    }
+    if (!__syncthreads_and(mbar_wait_bounded(&S.bar_mma, mma_done & 1, TMA_WAIT_CYCLES))) {
+      failed = 1;
+      wait_mma = 1;
+      if (more) wait_next = (1 - s) * 2 + (((k + 1) >> 1) & 1);
+      break;
+    }
+    ++mma_done;
     tc_fence_after();
-    tc_product(tmem + 16, smem_addr(S.a_hi), smem_addr(S.a_lo), smem_addr(S.b[2]),
-               smem_addr(S.b[3]));
-    tc_commit(&S.bar_mma);
-  }
-  if (ok) {
-    issued = 2;
-    ok = __syncthreads_and(mbar_wait_bounded(&S.bar_mma, 1, TMA_WAIT_CYCLES));
-  }
-  float df[16];
-  if (ok) {
-    tc_fence_after();
-    tc_ld16(tmem + ((unsigned)(warp * 32) << 16) + 16, df);
+    float df[16];
+    tc_ld16(trow + 16, df);
+
+    float cons[4] = {0.f, 0.f, 0.f, 0.f};
+    if (active) {
+      const unsigned cidx = (unsigned)y * pitch + (unsigned)x;
+      float acc[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc[i] = A.K.a0[i] * f[i] + df[i];
+      const bool b = !(c.rho > 0.f) ||
+                     ((__float_as_uint(c.rho + c.jx + c.jy + c.e) & 0x7f800000u) == 0x7f800000u);
+      bad |= b;
+      negT |= !b && !(q.P > 0.f);
+      cons[0] = c.rho; cons[1] = c.jx; cons[2] = c.jy; cons[3] = c.e;
+      neighbour_terms<float, unsigned, TC_BXP>(A, fin, ctr, PS, P, pitch, cidx, x, y, c, tnow, acc);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) fout[i * P + cidx] = acc[i];
+    }
+    if (audit) {  // per-tile partial (fixed order whatever the CTA)
+      const double v[4] = {widen(cons[0]), widen(cons[1]), widen(cons[2]), widen(cons[3])};
+      audit_tile<TC_N>(A, cur, v, S.red);
+    }
+    // stage s, the operand buffers and TMEM are free for the next tile
+    tc_fence_before();
+    __syncthreads();
   }
 
-  if (!ok) {
-    // A copy or an MMA did not finish in time: record it, wait once more
-    // (bounded) so nothing is left writing, free tensor memory, leave.
+  if (failed) {
+    // A copy or a product did not finish in time: record it, wait once more
+    // (bounded) for what this CTA issued, free tensor memory, leave.
     if (t == 0) {
       atomicExch(&A.st->tma_timeout, 1);
-      mbar_wait_bounded(&S.bar_tma, 0, TMA_WAIT_CYCLES);
-      if (issued >= 1) mbar_wait_bounded(&S.bar_mma, 0, TMA_WAIT_CYCLES);
-      if (issued >= 2) mbar_wait_bounded(&S.bar_mma, 1, TMA_WAIT_CYCLES);
+      if (wait_tma >= 0) mbar_wait_bounded(&S.bar_tma[wait_tma >> 1], wait_tma & 1, TMA_WAIT_CYCLES);
+      if (wait_next >= 0) mbar_wait_bounded(&S.bar_tma[wait_next >> 1], wait_next & 1, TMA_WAIT_CYCLES);
+      if (wait_mma) mbar_wait_bounded(&S.bar_mma, mma_done & 1, TMA_WAIT_CYCLES);
       audit_ticket_on_exit(A, audit);
     }
     tc_fence_before();
@@ -261,23 +310,6 @@ __global__ void __launch_bounds__(TC_N, 1)
     return;
   }
 
-  bool bad = false, negT = false;
-  float cons[4] = {0.f, 0.f, 0.f, 0.f};
-  if (active) {
-    const unsigned P = (unsigned)A.plane, pitch = (unsigned)A.pitch;
-    const unsigned cidx = (unsigned)y * pitch + (unsigned)x;
-    float acc[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = A.K.a0[i] * f[i] + df[i];
-    bad = !(c.rho > 0.f) || ((__float_as_uint(c.rho + c.jx + c.jy + c.e) & 0x7f800000u) == 0x7f800000u);
-    negT = !bad && !(press > 0.f);
-    cons[0] = c.rho; cons[1] = c.jx; cons[2] = c.jy; cons[3] = c.e;
-    neighbour_terms<float, unsigned, TC_BXP>(A, fin, ctr, PS, P, pitch, cidx, x, y, c,
-                                             A.dtr * (float)step, acc);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) fout[i * P + cidx] = acc[i];
-  }
-
   // free tensor memory (every tcgen05.ld of this CTA is complete)
   tc_fence_before();
   __syncthreads();
@@ -287,11 +319,7 @@ __global__ void __launch_bounds__(TC_N, 1)
                  : "memory");
 
   watchdog_flags(A.st, step, bad, negT);
-  if (audit) {  // one tile per CTA: partial index = block index
-    const double v[4] = {widen(cons[0]), widen(cons[1]), widen(cons[2]), widen(cons[3])};
-    audit_tile<TC_N>(A, blockIdx.y * gridDim.x + blockIdx.x, v, S.red);
-    audit_finish<TC_N>(A, step, S.red, &S.last);
-  }
+  if (audit) audit_finish<TC_N>(A, step, S.red, &S.last);
 }
 
 }  // namespace
@@ -330,10 +358,16 @@ void tc_prepare_constants(const double (&M)[16][16], const double (&Minv)[16][16
     }
 }
 
+cudaError_t tc_prepare() {
+  static_assert(sizeof(TcSmem) * TC_CTAS_PER_SM <= 220 * 1024,
+                "tensor-core step: TC_CTAS_PER_SM CTAs must fit in one SM's shared memory");
+  return cudaFuncSetAttribute(k_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(TcSmem));
+}
+
 cudaError_t tc_launch(const CUtensorMap& tm, const float* fin, float* fout,
                       const StepArgs<float>& A, const unsigned char* bconst, const float* wk,
                       dim3 grid, cudaStream_t s) {
-  static_assert(sizeof(TcSmem) <= 48 * 1024, "tensor-core step shared memory above 48 KB");
   k_step_tc<<<grid, TC_N, sizeof(TcSmem), s>>>(tm, fin, fout, A, bconst, wk);
   return cudaGetLastError();
 }

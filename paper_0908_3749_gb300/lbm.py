@@ -23,9 +23,9 @@ LBM_ERR_OOM = -4
 LBM_ERR_NONFINITE = -5
 LBM_ERR_TIMEOUT = -6
 
-LBM_FP64, LBM_FP32, LBM_TC_BF16X3, LBM_TC_TF32X3 = 0, 1, 2, 3
+LBM_FP64, LBM_FP32, LBM_TC_BF16X3, LBM_TC_TF32X3, LBM_DF64, LBM_FP32_DWMOM = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "tc_bf16x3": LBM_TC_BF16X3,
-              "tc_tf32x3": LBM_TC_TF32X3}
+              "tc_tf32x3": LBM_TC_TF32X3, "df64": LBM_DF64, "fp32_dwmom": LBM_FP32_DWMOM}
 BC = {"periodic": 0, "eq": 1, "reflect": 2, "extrap": 3, "wall": 4, "outflow": 5}
 AUDIT_RING = 1024
 

@@ -43,7 +43,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=WORKLOADS, default="reflection")
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--ny", type=int, default=None)
-    ap.add_argument("--precision", choices=("fp64", "fp32", "tc_tf32x3"), default="fp32")
+    ap.add_argument("--precision", choices=("fp64", "df64", "fp32", "fp32_dwmom", "tc_tf32x3"), default="fp32")
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--audit-every", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0,

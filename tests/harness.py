@@ -31,13 +31,24 @@ def gpu_run(w, nsteps, precision="fp64", audit_every=0, chunks=None, stream=None
             lbm.lbm_step(ctx, n)
         out = {k: np.empty((w.ny, w.nx)) for k in ("rho", "u", "v", "T")}
         lbm.lbm_moments(ctx, out["rho"], out["u"], out["v"], out["T"])
-        es = lbm.lbm_element_size(ctx)
-        f = np.empty((16, w.ny, w.nx), dtype=np.float64 if es == 8 else np.float32)
-        lbm.lbm_get_populations(ctx, f)
+        f = read_populations(lbm, ctx, w, precision)
         status = lbm.lbm_status(ctx)
     finally:
         lbm.lbm_destroy(ctx)
-    return out, f.astype(np.float64), status
+    return out, f, status
+
+
+def read_populations(lbm, ctx, w, precision):
+    """The context's populations as float64 (16, ny, nx); a double-word
+    checkpoint (precision "df64") holds a float pair (h, l) per population."""
+    if precision == "df64":
+        f = np.empty((16, w.ny, w.nx, 2), dtype=np.float32)
+        lbm.lbm_get_populations(ctx, f)
+        return f[..., 0].astype(np.float64) + f[..., 1].astype(np.float64)
+    es = lbm.lbm_element_size(ctx)
+    f = np.empty((16, w.ny, w.nx), dtype=np.float64 if es == 8 else np.float32)
+    lbm.lbm_get_populations(ctx, f)
+    return f.astype(np.float64)
 
 
 def oracle_run(w, nsteps):
@@ -63,6 +74,18 @@ def field_errors(got, ref):
 
 def fp64_tol(nsteps):
     return max(1e-12, 1e-14 * nsteps)
+
+
+# Unit roundoff of double-word arithmetic over that of FP64: 2^-48 / 2^-53.
+DW_OVER_FP64 = 32.0
+
+
+def df64_tol(nsteps):
+    """Bar of the double-word step (LBM_DF64) against the FP64 oracle: the
+    FP64 bar scaled by the ratio of the unit roundoffs, 2^-48 / 2^-53 = 32
+    (each double-word operation rounds at about 2^-48 of its operands where
+    FP64 rounds at 2^-53)."""
+    return DW_OVER_FP64 * fp64_tol(nsteps)
 
 
 def cancellation(f):
@@ -92,4 +115,4 @@ def pop_error(f, fref):
 
 
 __all__ = ["gpu_run", "oracle_run", "field_errors", "pop_error", "fp64_tol", "l1_errors", "W",
-           "cancellation", "fp64_tol_conditioned"]
+           "cancellation", "fp64_tol_conditioned", "df64_tol", "read_populations"]

@@ -6,9 +6,14 @@ Runs: the stable Sod tube of the first workload (200 x 4, dx = 0.005,
 dt = 1e-5, the paper's Sod rates x 0.4) to its last level 10 000, and the
 600 x 200 regular shock reflection (Sec. V.B.a geometry) to level 1000.
 Both sides start from the same initial populations and are compared at
-levels 1, 10, 100, 1000 (and 10 000 for the tube). The bar is 1e-12 at
-every level up to 100 and harness.fp64_tol beyond (the oracle's own FP64
-rounding drift, about 1e-14 per step against an extended-precision run).
+levels 1, 10, 100, 1000 (and 10 000 for the tube). Measured on GB300
+(relative L-infinity, worst field): Sod 5.1e-15 / 5.1e-15 / 9.4e-15 /
+5.1e-14 / 6.2e-13 at levels 1 / 10 / 100 / 1000 / 10 000; reflection
+1.9e-14 / 6.6e-14 / 3.8e-13 / 3.9e-12 at 1 / 10 / 100 / 1000. The bar is
+therefore 1e-12 at every level of the Sod run, and for the reflection 1e-12
+up to level 100 and harness.fp64_tol beyond (the oracle's own FP64 rounding
+drift, about 1e-14 per step against an extended-precision run, which the
+supersonic reflection reaches first).
 """
 import numpy as np
 import pytest
@@ -48,17 +53,17 @@ def _curve(w, levels, precision="fp64"):
     return rows
 
 
-def _assert_bar(rows, name):
+def _assert_bar(rows, name, fixed_until):
     for level, err in rows:
-        bar = 1e-12 if level <= 100 else fp64_tol(level)
+        bar = 1e-12 if level <= fixed_until else fp64_tol(level)
         assert max(err.values()) <= bar, (name, level, err, bar)
 
 
 def test_error_growth_sod_stable_to_10000():
     w = W.sod_config1("stable", ny=4)
-    _assert_bar(_curve(w, [1, 10, 100, 1000, 10000]), w.name)
+    _assert_bar(_curve(w, [1, 10, 100, 1000, 10000]), w.name, fixed_until=10000)
 
 
 def test_error_growth_regular_reflection_to_1000():
     w = W.regular_reflection()
-    _assert_bar(_curve(w, [1, 10, 100, 1000]), w.name)
+    _assert_bar(_curve(w, [1, 10, 100, 1000]), w.name, fixed_until=100)

@@ -135,3 +135,50 @@ def test_tube_batch_full_size_sampled():
     print("tube batch (4096 tubes, %d steps): %d sampled tubes checked, worst field error %.3g"
           % (n, checked, worst))
     assert checked >= 40
+
+
+def test_tube_batch_unstable_tubes_fail_in_the_oracle_too():
+    """The batch's watchdog flags some tubes of the 4096 as non-physical
+    (rho <= 0 or non-finite): the strongest Riemann problems of the
+    configuration's distribution, which the scheme itself cannot hold at
+    these rates and spacings. After 300 steps, a seeded sample of 24 flagged
+    tubes fails in the oracle too, at the same time level (within one: the
+    watchdog checks each step's input), and a sample of 16 unflagged tubes
+    stays physical in the oracle with the same fields."""
+    from paper_0908_3749_gb300 import lbm
+    B = W.tube_batch()
+    nt = len(B["nx"])
+    n = 300
+    b = lbm.lbm_batch_create(B["nx"], B["dx"], B["dt"], B["s"], B["left"], B["right"])
+    try:
+        lbm.lbm_batch_set_init(b, *W.tube_fields(B))
+        lbm.lbm_batch_step(b, n)
+        tot = lbm.lbm_batch_total_nodes(b)
+        out = [np.empty(tot) for _ in range(4)]
+        lbm.lbm_batch_moments(b, *out)
+        rc, bad, nbad, to = lbm.lbm_batch_status(b, nt)
+    finally:
+        lbm.lbm_batch_destroy(b)
+    assert to == 0 and nbad > 0
+    offs = np.concatenate([[0], np.cumsum(B["nx"])])
+    rng = np.random.default_rng(300)
+    flagged = rng.choice(np.nonzero(bad >= 0)[0], 24, replace=False)
+    clean = rng.choice(np.nonzero(bad < 0)[0], 16, replace=False)
+    for t in list(flagged) + list(clean):
+        nx = int(B["nx"][t])
+        x = (np.arange(nx) + 0.5) / nx
+        f = [np.where(x <= 0.5, B["left"][t, q], B["right"][t, q])[None, :] for q in range(4)]
+        bc = (("eq", tuple(B["left"][t])), ("eq", tuple(B["right"][t])),
+              ("periodic", None), ("periodic", None))
+        w = W.Workload("tube%d" % t, nx, 1, B["dx"][t], B["dx"][t], B["dt"], tuple(B["s"][t]), bc, *f)
+        fo, first_bad = scheme.run(scheme.init_populations(*w.fields()), w.cfg(), n, check_every=1)
+        if bad[t] >= 0:
+            assert first_bad is not None and abs(int(bad[t]) - first_bad) <= 1, (t, bad[t], first_bad)
+        else:
+            assert first_bad is None, (t, first_bad)
+            rho, u, v, T = scheme.macroscopic(fo)
+            got = {k: out[q][offs[t]:offs[t + 1]][None, :] for q, k in enumerate(("rho", "u", "v", "T"))}
+            err = max(field_errors(got, {"rho": rho, "u": u, "v": v, "T": T}).values())
+            assert err <= 1e-3, (t, err)
+    print("tube batch, %d steps: %d of %d tubes flagged; 24 flagged and 16 clean sampled, "
+          "the oracle agrees" % (n, nbad, nt))

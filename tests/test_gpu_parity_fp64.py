@@ -60,8 +60,9 @@ def test_sod_config1_literal_1000_steps():
 
 
 def test_sod_config1_stable_full_run():
+    """All 10 000 steps within 1e-12 (measured 6.2e-13, test_gpu_error_growth)."""
     w = W.sod_config1("stable", ny=4)
-    _check(w, w.nsteps)
+    _check(w, w.nsteps, tol=1e-12)
 
 
 @pytest.mark.parametrize("nsteps", [1, 10, 100])
