@@ -22,8 +22,9 @@ the FP64 fused multiply-add rate measured in this run
 
 Lines printed (rank 0): one JSON object. Besides the contract keys:
 ``df64_large_grid`` is the double-word step (FP32 pairs, ~48-bit
-arithmetic on the FP32 units), ``fp32_large_grid``, ``tensor_core_tf32x3``
-and ``fp32_two_steps_per_launch`` the FP32 steps, all on the same grid
+arithmetic on the FP32 units), ``fp32_large_grid``,
+``fp32_dwmom_large_grid`` (double-word conserved moments and equilibria),
+``tensor_core_tf32x3`` and ``fp32_two_steps_per_launch`` the FP32 steps, all on the same grid
 (64-step CUDA-graph replays back to back) with their errors against an FP64
 GPU run; ``reflection_600x200`` the 600 x 200 regular shock reflection
 (Sec. V.B.a geometry) in FP64 and FP32, each step timed alone with the L2
@@ -377,6 +378,7 @@ def large_grid_measure(torch, lbm, stream, audit_every, hbm_peak):
     lbm.lbm_destroy(c64)
     for prec, key, fused in (("df64", "df64_large_grid", False),
                              ("fp32", "fp32_large_grid", False),
+                             ("fp32_dwmom", "fp32_dwmom_large_grid", False),
                              ("tc_tf32x3", "tensor_core_tf32x3", False),
                              ("fp32", "fp32_two_steps_per_launch", True)):
         ctx = make_ctx(lbm, wl, prec, 0, stream, tune=not fused)
@@ -402,6 +404,9 @@ def large_grid_measure(torch, lbm, stream, audit_every, hbm_peak):
                     "frac_of_hbm": gbs / hbm_peak, "step_blocks": blocks,
                     "timing": "64-step CUDA-graph replays back to back (inputs larger than L2)",
                     "error_vs_fp64_gpu_after_%d_steps" % nsteps: err, "status": list(st)}
+        if prec == "fp32_dwmom":
+            out[key]["note"] = ("FP32 step with the conserved moments, Eq. 14 equilibria and "
+                                "temperature in double-word arithmetic (LBM_FP32_DWMOM)")
         if prec == "df64":
             out[key]["dtype"] = "f32 double-word (h + l)"
             out[key]["fp64_equivalent_tflops"] = FLOPS_PER_CELL * cl / (ms * 1e-3) / 1e12

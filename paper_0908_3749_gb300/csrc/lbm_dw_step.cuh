@@ -14,7 +14,9 @@
 //   the Eq. 14 equilibria from (rho, j, e); the deviations m_k - m_k^eq;
 //   the back-map M^-1 (-dt S_hat (m - m^eq)) through the scaled block
 //   inverses (constants of Coeffs<dw>) and the inverse 4-point transform;
-//   the update a0 f + df + aW f(x-dx) + aE f(x+dx) + aS f(y-dy) + aN f(y+dy).
+//   the update f + [df + aW (f(x-dx) - f) + aE (f(x+dx) - f) + aS (f(y-dy) - f)
+//   + aN (f(y+dy) - f)] (Eq. A.1 with a0 = 1 - aW - aE - aS - aN, in increment
+//   form so that rounding scales with the change of f).
 #pragma once
 
 #include <type_traits>
@@ -300,12 +302,15 @@ __device__ __forceinline__ void dw_ghost(const StepArgs<dw>& A, const dw* __rest
   dw_feq(A.K, A.K3, rho, jx, jy, e, g);
 }
 
-// acc[i] += aW f(x-dx) + aE f(x+dx) + aS f(y-dy) + aN f(y+dy) for an edge node
-// (its tile pointer ctr, global index c, conserved moments m at time t).
+// acc[i] += aW (f(x-dx) - f) + aE (f(x+dx) - f) + aS (f(y-dy) - f) +
+// aN (f(y+dy) - f) for an edge node with populations f (its tile pointer
+// ctr, global index c, conserved moments m at time t): the increment form
+// of the interior update.
 template <typename Off, int BXP>
 __device__ __forceinline__ void dw_edge_terms(const StepArgs<dw>& A, const dw* __restrict__ fin,
                                               const dw* ctr, int PS, Off P, Off pitch, Off c, int x,
                                               int y, const DWf (&m)[4], dw t, DWf (&acc)[16]) {
+  auto f = [&](int i) { return dwf(ctr[i * PS]); };  // the node's own populations
   // side: 0 x-, 1 x+, 2 y-, 3 y+ ; the neighbour lies inside when the node
   // is not on that side
   const bool inside[4] = {x > 0, x < A.nx - 1, y > 0, y < A.ny - 1};
@@ -323,12 +328,13 @@ __device__ __forceinline__ void dw_edge_terms(const StepArgs<dw>& A, const dw* _
     if (inside[side]) {
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        if (use(i)) acc[i] = dadd(acc[i], dmulk(dwf(ctr[i * PS + toff[side]]), wgt[i], wgt3[i]));
+        if (use(i))
+          acc[i] = dadd(acc[i], dmulk(dsub(dwf(ctr[i * PS + toff[side]]), f(i)), wgt[i], wgt3[i]));
     } else if (A.bc[side] == LBM_BC_PERIODIC) {
       const Off n = c + wrap[side];
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        if (use(i)) acc[i] = dadd(acc[i], dmulk(dwf(fin[i * P + n]), wgt[i], wgt3[i]));
+        if (use(i)) acc[i] = dadd(acc[i], dmulk(dsub(dwf(fin[i * P + n]), f(i)), wgt[i], wgt3[i]));
     } else {
       DWf g[16];
       float gt[16];
@@ -336,9 +342,9 @@ __device__ __forceinline__ void dw_edge_terms(const StepArgs<dw>& A, const dw* _
 #pragma unroll
       for (int i = 0; i < 16; ++i)
         if (use(i)) {
-          DWf p = dmulk(g[i], wgt[i], wgt3[i]);
-          p.l = lfma(wgt[i].h, gt[i], p.l);   // the ghost's third word
-          acc[i] = dadd(acc[i], p);
+          DWf d = dsub(g[i], f(i));
+          d.l = ladd(d.l, gt[i]);   // the ghost's third word
+          acc[i] = dadd(acc[i], dmulk(d, wgt[i], wgt3[i]));
         }
     }
   }
@@ -429,16 +435,21 @@ __device__ __forceinline__ void step_tile_dw(const StepArgs<dw>& A, const dw* __
     if (inner) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        DW<V> a = dadd(dmulk(ld(i), A.K.a0[i], A.K3.a0[i]), df[i]);
+        // f+ = f + [df + sum_n a_n (f_n - f)]: the Lax-Wendroff update of
+        // Eq. A.1 in increment form (a0 = 1 - sum_n a_n), so that rounding
+        // scales with the change of f, not with f (populations reach 50 rho
+        // in supersonic flow), and a uniform state stays uniform.
+        const DW<V> fi = ld(i);
+        DW<V> a = df[i];
         if (has_x(i)) {
-          a = dadd(a, dmulk(ldn<V>(sa, sb, i * PS - 1), A.K.aW[i], A.K3.aW[i]));
-          a = dadd(a, dmulk(ldn<V>(sa, sb, i * PS + 1), A.K.aE[i], A.K3.aE[i]));
+          a = dadd(a, dmulk(dsub(ldn<V>(sa, sb, i * PS - 1), fi), A.K.aW[i], A.K3.aW[i]));
+          a = dadd(a, dmulk(dsub(ldn<V>(sa, sb, i * PS + 1), fi), A.K.aE[i], A.K3.aE[i]));
         }
         if (has_y(i)) {
-          a = dadd(a, dmulk(ldn<V>(sa, sb, i * PS - BXP), A.K.aS[i], A.K3.aS[i]));
-          a = dadd(a, dmulk(ldn<V>(sa, sb, i * PS + BXP), A.K.aN[i], A.K3.aN[i]));
+          a = dadd(a, dmulk(dsub(ldn<V>(sa, sb, i * PS - BXP), fi), A.K.aS[i], A.K3.aS[i]));
+          a = dadd(a, dmulk(dsub(ldn<V>(sa, sb, i * PS + BXP), fi), A.K.aN[i], A.K3.aN[i]));
         }
-        a = dnorm(a);
+        a = dnorm(dadd(fi, a));
 #pragma unroll
         for (int k = 0; k < NL; ++k) fout[i * P + c0 + (Off)(k * TY) * pitch] = lane(a, k);
       }
@@ -448,14 +459,14 @@ __device__ __forceinline__ void step_tile_dw(const StepArgs<dw>& A, const dw* __
         if (!act[k]) continue;
         DWf acc1[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          acc1[i] = lane_dw(dadd(dmulk(ld(i), A.K.a0[i], A.K3.a0[i]), df[i]), k);
+        for (int i = 0; i < 16; ++i) acc1[i] = lane_dw(df[i], k);
         const DWf mk[4] = {dwf(mc[k][0]), dwf(mc[k][1]), dwf(mc[k][2]), dwf(mc[k][3])};
         const Off ck = c0 + (Off)(k * TY) * pitch;
-        dw_edge_terms<Off, BXP>(A, fin, k == 0 ? sa : sb, PS, P, pitch, ck, x, y[k], mk, t, acc1);
+        const dw* ctrk = k == 0 ? sa : sb;
+        dw_edge_terms<Off, BXP>(A, fin, ctrk, PS, P, pitch, ck, x, y[k], mk, t, acc1);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const DWf a = dnorm(acc1[i]);
+          const DWf a = dnorm(dadd(dwf(ctrk[i * PS]), acc1[i]));
           fout[i * P + ck] = dw(a.h, a.l);
         }
       }

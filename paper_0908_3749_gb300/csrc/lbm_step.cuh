@@ -50,9 +50,14 @@ template <> struct Shape<double> {
 #ifndef LBM_DW_LANES
 #define LBM_DW_LANES 1
 #endif
+// Blocks per SM of the one-tile double-word form (4: 128 registers, no
+// spills; 5 spills in the node update).
+#ifndef LBM_DW_MINB
+#define LBM_DW_MINB 4
+#endif
 template <> struct Shape<dw> {
   static constexpr int X = 32, Y = 4, TY = Y / LBM_DW_LANES;
-  static constexpr int MINB = LBM_DW_LANES == 1 ? 5 : 6, MINB_PIPE = LBM_DW_LANES == 1 ? 3 : 3;
+  static constexpr int MINB = LBM_DW_LANES == 1 ? LBM_DW_MINB : 6, MINB_PIPE = 3;
   static_assert(LBM_DW_LANES == 1 || LBM_DW_LANES == 2, "one or two nodes per thread");
 };
 constexpr int AUX_X = 32, AUX_Y = 8, AUX_N = AUX_X * AUX_Y;  // init / moments / audit
