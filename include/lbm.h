@@ -56,7 +56,7 @@ enum lbm_precision {
                         tensor-core products (reserved: LBM_ERR_UNSUPPORTED) */
   LBM_TC_TF32X3 = 3, /* FP32 populations; m = M f and the back-map M^-1 as
                         3xTF32 tensor-core products (tcgen05, FP32
-                        accumulation) over 128-node tiles; equilibria,
+                        accumulation) over 32 x 8 node tiles; equilibria,
                         Lax-Wendroff update, moments and audits as LBM_FP32.
                         Grids with 16 x pitch x ny >= 2^32 elements are
                         LBM_ERR_UNSUPPORTED. */
@@ -207,7 +207,7 @@ int lbm_element_size(lbm_ctx* ctx);
  * is the same, audit partials are kept per tile); only the speed does.
  *  lbm_set_step_blocks: 0 = the default, one block per tile; larger values
  *    are capped at the number of tiles. Synchronises; LBM_ERR_UNSUPPORTED
- *    for LBM_TC_TF32X3 (one CTA per 128-node tile).
+ *    for LBM_TC_TF32X3 (its own persistent grid, 4 CTAs per multiprocessor).
  *  lbm_step_blocks: the current value (-1 for a NULL ctx).
  *  lbm_autotune: times `launches` step launches for each candidate (one
  *    block per tile; 1 .. k blocks per multiprocessor; ceil(tiles / m) blocks

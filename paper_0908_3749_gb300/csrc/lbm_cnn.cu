@@ -10,19 +10,23 @@
 // once per update into [COUT][K] BF16 (K contiguous, the "col" operand) for
 // the forward pass and into the tap-flipped, channel-transposed [CIN][K'] for
 // the input-gradient pass, which is the same GEMM run on the output
-// gradients. Weight gradients are FP32 sums over pixels on the CUDA cores
-// (per-block partials, then a fixed-order sum: reproducible). Adam keeps FP32
+// gradients. Weight gradients are contractions over the pixels on the
+// 5th-generation tensor cores (tcgen05, BF16 inputs, FP32 accumulation in
+// tensor memory; the first layer's FP32 features as three BF16 parts), as
+// per-CTA partials, then a fixed-order sum (reproducible). Adam keeps FP32
 // master weights.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>  // header-only; ranges cost nothing without a profiler attached
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "../../include/lbm_cnn.h"
+#include "tc05.cuh"
 
 namespace {
 
@@ -134,50 +138,320 @@ __global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Weight and bias gradients (FP32 CUDA cores, per-block partials)
+// Weight and bias gradients on the tensor cores (tcgen05)
 // ---------------------------------------------------------------------------
-// Thread t < 9 CIN owns the pair (tap, ci) and all COUT outputs
-// dW[tap][ci][co] = sum_p act[p + off(tap)][ci] dz[p][co]; thread 9 CIN + co
-// (co < COUT) owns db[co] = sum_p dz[p][co]. Block b sums pixels
-// [b * chunk, (b + 1) * chunk).
-__device__ __forceinline__ float to_f32(float a) { return a; }
-__device__ __forceinline__ float to_f32(__nv_bfloat16 a) { return __bfloat162float(a); }
+// dW[tap][ci][co] = sum_p act[p + off(tap)][ci] dz[p][co] is a contraction
+// over the pixels: D (M x N) = A (M x K) B (K x N) with K = the pixels, N =
+// the output channels (32, or 4 padded to 16 with zero rows of B) and the
+// rows m of A:
+//   32-channel layers (BF16 activations): m = tap * 32 + ci, 288 rows as
+//     three M = 128 tiles (taps 0-3, taps 4-7, tap 8 and 96 zero rows);
+//   first layer (FP32 features, 4 channels): each feature split into three
+//     BF16 parts x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 =
+//     bf16(x - x0 - x1), the differences exact in FP32; 24 significant bits
+//     together), m = part * 36 + tap * 4 + ci, 108 rows of one M = 128 tile;
+//     the epilogue adds the three parts' sums (x2 first), which gives the
+//     contraction of the FP32 features.
+// Persistent CTAs of 128 threads take chunks of WG_CHUNK pixels (WG_CHUNK /
+// 16 MMA steps of K = 16): the threads gather the chunk's shifted features
+// and output gradients as blocks of 8 channels x 8 consecutive pixels (eight
+// 16-byte loads, one per pixel, transposed in registers by byte permutes)
+// and store them in the canonical K-major layout; one thread issues the
+// chunk's MMAs into the CTA's TMEM accumulators and commits them to an
+// mbarrier, which every thread waits for (bounded) before the next chunk is
+// gathered. At the end each thread reads its rows of the accumulators
+// (tcgen05.ld) into the CTA's partial sums, with the bias gradient (sum_p
+// dz[p][co], FP32, a fixed order); k_sum_partials adds the partials of all
+// CTAs in a fixed order.
+constexpr int WG_T = 128, WG_CHUNK = 64, WG_KS = WG_CHUNK / 16;
+constexpr int WG_CTAS_PER_SM = 4;
+constexpr unsigned WG_TMEM_COLS = 128;
+constexpr unsigned WG_A_TILE = 128 * 16 * 2;  // one M tile x one K step, BF16 (4 KB)
 
-template <int CIN, int COUT, typename TA>
-__global__ void k_wgrad(const TA* __restrict__ act, const __nv_bfloat16* __restrict__ dz,
-                        int H, int W, int chunk, float* __restrict__ partial) {
-  const int t = threadIdx.x;
-  constexpr int NW = 9 * CIN * COUT, NOUT = NW + COUT;
-  float acc[COUT];
+template <int CIN>
+__host__ __device__ constexpr int wg_mt() { return CIN == 32 ? 3 : 1; }  // M tiles
+
+template <int CIN, int NP>
+struct WgSmem {
+  unsigned char a[wg_mt<CIN>() * WG_KS][WG_A_TILE];  // reused by the epilogue
+  unsigned char b[WG_KS][NP * 16 * 2];                // reused for the bias sums
+  unsigned long long bar;
+  unsigned tmem;
+};
+
+// Byte offset of element (row, k) of a rows x 16 BF16 operand tile in the
+// canonical K-major layout without swizzle (core matrices of 8 rows x 8
+// elements, 128 contiguous bytes; the next core matrix along K 128 bytes on,
+// the next 8-row group 256 bytes on).
+__device__ __forceinline__ unsigned wg_off(int row, int k) {
+  return (unsigned)((row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Transposes 8 pixels x 8 channels (v[j] = channels 0..7 of pixel j, two per
+// word) into 8 rows (channels) of 8 pixels: out[c] = pixels 0..7 of channel c.
+__device__ __forceinline__ void wg_transpose8(const uint4 (&v)[8], uint4 (&out)[8]) {
 #pragma unroll
-  for (int c = 0; c < COUT; ++c) acc[c] = 0.f;
-  const int npix = H * W;
-  const int pbeg = blockIdx.x * chunk, pend = min(npix, pbeg + chunk);
-  const bool wthread = t < 9 * CIN;
-  const bool bthread = t >= 9 * CIN && t < 9 * CIN + COUT;
-  const int tap = wthread ? t / CIN : 0, ci = wthread ? t % CIN : 0;
-  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-  for (int p = pbeg; p < pend; ++p) {
-    const int y = p / W, x = p - y * W;
-    if (wthread) {
-      const int yy = y + dy, xx = x + dx;
-      float a = 0.f;
-      if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-        a = to_f32(act[((long long)yy * W + xx) * CIN + ci]);
+  for (int cp = 0; cp < 4; ++cp) {
+    unsigned lo[4], hi[4];
 #pragma unroll
-      for (int c = 0; c < COUT; ++c) acc[c] += a * __bfloat162float(dz[(long long)p * COUT + c]);
-    } else if (bthread) {
-      acc[0] += __bfloat162float(dz[(long long)p * COUT + (t - 9 * CIN)]);
+    for (int pp = 0; pp < 4; ++pp) {
+      const unsigned a = (&v[2 * pp].x)[cp], b = (&v[2 * pp + 1].x)[cp];
+      lo[pp] = __byte_perm(a, b, 0x5410);  // channel 2 cp of pixels 2 pp, 2 pp + 1
+      hi[pp] = __byte_perm(a, b, 0x7632);  // channel 2 cp + 1
     }
-  }
-  float* out = partial + (long long)blockIdx.x * NOUT;
-  if (wthread) {
-#pragma unroll
-    for (int c = 0; c < COUT; ++c) out[(tap * CIN + ci) * COUT + c] = acc[c];
-  } else if (bthread) {
-    out[NW + (t - 9 * CIN)] = acc[0];
+    out[2 * cp] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    out[2 * cp + 1] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
   }
 }
+
+__device__ __forceinline__ float bf_lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(unsigned w) { return __uint_as_float(w & 0xFFFF0000u); }
+__device__ __forceinline__ unsigned bf_bits(__nv_bfloat16 h) {
+  return (unsigned)__bfloat16_as_ushort(h);
+}
+
+// The three BF16 parts of x (bit patterns).
+__device__ __forceinline__ void split3(float x, unsigned (&p)[3]) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h0);
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+  p[0] = bf_bits(h0);
+  p[1] = bf_bits(h1);
+  p[2] = bf_bits(h2);
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WG_T, WG_CTAS_PER_SM)
+    k_wgrad_tc(const void* __restrict__ act_, const __nv_bfloat16* __restrict__ dz, int H, int W,
+               float* __restrict__ partial) {
+  constexpr int NP = COUT == 32 ? 32 : 16;  // N of the MMA
+  constexpr int MT = wg_mt<CIN>();
+  constexpr int ROWS = CIN == 32 ? 9 * 32 : 3 * 36;  // used rows of A
+  constexpr int NOUT = 9 * CIN * COUT + COUT;
+  constexpr unsigned IDESC = tc05::idesc_f32acc(tc05::FMT_BF16, 128, NP);
+  static_assert(CIN == 32 || (CIN == 4 && COUT == 32), "layer shapes of the corrector");
+  extern __shared__ __align__(1024) unsigned char wg_raw[];
+  WgSmem<CIN, NP>& S = *reinterpret_cast<WgSmem<CIN, NP>*>(wg_raw);
+  const int t = threadIdx.x, warp = t >> 5;
+  const int npix = H * W, nchunks = (npix + WG_CHUNK - 1) / WG_CHUNK;
+  if (warp == 0) tc05::alloc(&S.tmem, WG_TMEM_COLS);
+  if (t == 0) gbtma::mbar_init(&S.bar, 1);
+  // Zero the rows that no gather writes: A rows ROWS .. MT * 128 - 1 (in the
+  // last M tile), B rows COUT .. NP - 1.
+  constexpr int AZ = MT * 128 - ROWS, AZ0 = 128 - AZ;
+  for (int i = t; i < WG_KS * AZ * 2; i += WG_T) {
+    const int ks = i / (AZ * 2), r = AZ0 + (i % (AZ * 2)) / 2, half = i & 1;
+    *reinterpret_cast<uint4*>(&S.a[(MT - 1) * WG_KS + ks][wg_off(r, 8 * half)]) = make_uint4(0, 0, 0, 0);
+  }
+  for (int i = t; i < WG_KS * (NP - COUT) * 2; i += WG_T) {
+    const int ks = i / ((NP - COUT) * 2), r = COUT + (i % ((NP - COUT) * 2)) / 2, half = i & 1;
+    *reinterpret_cast<uint4*>(&S.b[ks][wg_off(r, 8 * half)]) = make_uint4(0, 0, 0, 0);
+  }
+  tc05::fence_before();
+  __syncthreads();
+  tc05::fence_after();
+  const unsigned tmem = S.tmem;
+
+  float db[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // bias sums of this thread's B block
+  constexpr int NBB = COUT == 32 ? 32 : 8;                 // B blocks per chunk
+  unsigned done = 0;                                      // chunks whose MMAs completed
+  bool ok = true;
+  for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int pbase = ch * WG_CHUNK;
+    if constexpr (CIN == 32) {
+      // A: 288 blocks (tap, pixel group of 8, channel group of 8), channel
+      // group fastest so that neighbouring threads read one pixel's 64 bytes.
+      const __nv_bfloat16* act = static_cast<const __nv_bfloat16*>(act_);
+      for (int q = t; q < 288; q += WG_T) {
+        const int cg = q & 3, pg = (q >> 2) & 7, tap = q >> 5;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        uint4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int p = pbase + pg * 8 + j;
+          const int y = p / W, x = p - y * W, yy = y + dy, xx = x + dx;
+          v[j] = (p < npix && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                     ? __ldg(reinterpret_cast<const uint4*>(act + ((long long)yy * W + xx) * 32 + cg * 8))
+                     : make_uint4(0, 0, 0, 0);
+        }
+        uint4 o[8];
+        wg_transpose8(v, o);
+        const int mt = tap < 8 ? tap / 4 : 2, rbase = (tap < 8 ? (tap % 4) * 32 : 0) + cg * 8;
+        unsigned char* tile = S.a[mt * WG_KS + pg / 2];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          *reinterpret_cast<uint4*>(tile + wg_off(rbase + c, (pg & 1) * 8)) = o[c];
+      }
+    } else {
+      // A: 72 blocks (tap, pixel group of 8): 8 pixels x 4 features, each
+      // split into three BF16 parts, give rows part * 36 + tap * 4 + ci.
+      const float* act = static_cast<const float*>(act_);
+      if (t < 72) {
+        const int pg = t & 7, tap = t >> 3;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        unsigned part[8][4][3];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int p = pbase + pg * 8 + j;
+          const int y = p / W, x = p - y * W, yy = y + dy, xx = x + dx;
+          const float4 v = (p < npix && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                               ? __ldg(reinterpret_cast<const float4*>(act + ((long long)yy * W + xx) * 4))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+          split3(v.x, part[j][0]);
+          split3(v.y, part[j][1]);
+          split3(v.z, part[j][2]);
+          split3(v.w, part[j][3]);
+        }
+        unsigned char* tile = S.a[pg / 2];
+#pragma unroll
+        for (int pt = 0; pt < 3; ++pt)
+#pragma unroll
+          for (int ci = 0; ci < 4; ++ci) {
+            uint4 o;
+            o.x = part[0][ci][pt] | (part[1][ci][pt] << 16);
+            o.y = part[2][ci][pt] | (part[3][ci][pt] << 16);
+            o.z = part[4][ci][pt] | (part[5][ci][pt] << 16);
+            o.w = part[6][ci][pt] | (part[7][ci][pt] << 16);
+            *reinterpret_cast<uint4*>(tile + wg_off(pt * 36 + tap * 4 + ci, (pg & 1) * 8)) = o;
+          }
+      }
+    }
+    // B: the output gradients of the chunk's pixels (and the bias sums).
+    if (t < NBB) {
+      const int pg = COUT == 32 ? t >> 2 : t, cg = COUT == 32 ? t & 3 : 0;
+      unsigned char* tile = S.b[pg / 2];
+      if constexpr (COUT == 32) {
+        uint4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int p = pbase + pg * 8 + j;
+          v[j] = p < npix ? __ldg(reinterpret_cast<const uint4*>(dz + (long long)p * 32 + cg * 8))
+                          : make_uint4(0, 0, 0, 0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const unsigned w = (&v[j].x)[c];
+            db[2 * c] += bf_lo(w);
+            db[2 * c + 1] += bf_hi(w);
+          }
+        }
+        uint4 o[8];
+        wg_transpose8(v, o);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          *reinterpret_cast<uint4*>(tile + wg_off(cg * 8 + c, (pg & 1) * 8)) = o[c];
+      } else {
+        uint2 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int p = pbase + pg * 8 + j;
+          v[j] = p < npix ? __ldg(reinterpret_cast<const uint2*>(dz + (long long)p * 4))
+                          : make_uint2(0, 0);
+          db[0] += bf_lo(v[j].x);
+          db[1] += bf_hi(v[j].x);
+          db[2] += bf_lo(v[j].y);
+          db[3] += bf_hi(v[j].y);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          unsigned w[4];
+#pragma unroll
+          for (int pp = 0; pp < 4; ++pp) {
+            const unsigned a = (&v[2 * pp].x)[c >> 1], b = (&v[2 * pp + 1].x)[c >> 1];
+            w[pp] = __byte_perm(a, b, (c & 1) ? 0x7632 : 0x5410);
+          }
+          *reinterpret_cast<uint4*>(tile + wg_off(c, (pg & 1) * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+    }
+    tc05::fence_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc05::fence_after();
+#pragma unroll
+      for (int ks = 0; ks < WG_KS; ++ks)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+          tc05::mma_f16(tmem + mt * NP,
+                        tc05::smem_desc(gbtma::smem_addr(S.a[mt * WG_KS + ks]), 128, 256),
+                        tc05::smem_desc(gbtma::smem_addr(S.b[ks]), 128, 256), IDESC,
+                        (done > 0 || ks > 0) ? 1u : 0u);
+      tc05::commit(&S.bar);
+    }
+    ok = __syncthreads_and(gbtma::mbar_wait_bounded(&S.bar, done & 1, gbtma::TMA_WAIT_CYCLES));
+    if (!ok) break;
+    ++done;
+    tc05::fence_after();
+  }
+  if (!ok) {
+    // The products did not complete in time: wait once more (bounded), mark
+    // this CTA's partials not-a-number (the training loss turns non-finite
+    // and the host reports it), free tensor memory.
+    if (t == 0) gbtma::mbar_wait_bounded(&S.bar, done & 1, gbtma::TMA_WAIT_CYCLES);
+    for (int i = t; i < NOUT; i += WG_T) partial[(long long)blockIdx.x * NOUT + i] = __int_as_float(0x7fc00000);
+    tc05::fence_before();
+    __syncthreads();
+    if (warp == 0) tc05::dealloc(tmem, WG_TMEM_COLS);
+    return;
+  }
+  float* out = partial + (long long)blockIdx.x * NOUT;
+  if constexpr (CIN == 32) {
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      const int row = mt * 128 + t;  // = tap * 32 + ci
+#pragma unroll
+      for (int cb = 0; cb < NP / 16; ++cb) {
+        float v[16];
+        tc05::ld16(tmem + ((unsigned)(warp * 32) << 16) + mt * NP + cb * 16, v);
+        if (row < ROWS)
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (cb * 16 + c < COUT) out[row * COUT + cb * 16 + c] = done ? v[c] : 0.f;
+      }
+    }
+  } else {
+    // rows of the three parts through shared memory (the A tiles are free:
+    // every product has completed), then out[r][co] = D2 + D1 + D0.
+    float* sD = reinterpret_cast<float*>(S.a[0]);  // 128 x 32 FP32 = 16 KB
+    static_assert(sizeof(S.a) >= 128 * 32 * sizeof(float), "epilogue scratch");
+#pragma unroll
+    for (int cb = 0; cb < 2; ++cb) {
+      float v[16];
+      tc05::ld16(tmem + ((unsigned)(warp * 32) << 16) + cb * 16, v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) sD[t * 32 + ((cb * 16 + c + t) & 31)] = done ? v[c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = t; i < 36 * 32; i += WG_T) {
+      const int r = i >> 5, co = i & 31;
+      auto at = [&](int row) { return sD[row * 32 + ((co + row) & 31)]; };
+      out[r * 32 + co] = (at(72 + r) + at(36 + r)) + at(r);
+    }
+  }
+  // bias: thread t (t < NBB) holds 8 (COUT 32) or 4 (COUT 4) channel sums of
+  // pixel group pg; add the pixel groups in order.
+  float* sdb = reinterpret_cast<float*>(S.b[0]);  // the B tiles are free now
+  tc05::fence_before();
+  __syncthreads();
+  if (t < NBB)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sdb[t * 8 + c] = db[c];
+  __syncthreads();
+  if (t < COUT) {
+    float s = 0.f;
+    if constexpr (COUT == 32) {
+      const int cg = t >> 3, c = t & 7;
+      for (int pg = 0; pg < 8; ++pg) s += sdb[(pg * 4 + cg) * 8 + c];
+    } else {
+      for (int pg = 0; pg < 8; ++pg) s += sdb[pg * 8 + t];
+    }
+    out[9 * CIN * COUT + t] = s;
+  }
+  if (warp == 0) tc05::dealloc(tmem, WG_TMEM_COLS);
+}
+
+template <int CIN, int COUT>
+constexpr size_t wg_smem() { return sizeof(WgSmem<CIN, COUT == 32 ? 32 : 16>); }
 
 // First layer (4 -> 32 channels) in FP32 on the CUDA cores, straight from the
 // FP32 input features [p][4]: 3 x 3 correlation with zero padding, bias,
@@ -428,7 +702,7 @@ struct lbm_cnn {
   float* wpartial = nullptr;    // weight-gradient partials
   double* dpart = nullptr;      // loss / mass partials
   double* dloss = nullptr;
-  int wchunk = 0, wblocks = 0;
+  int wblocks = 0;              // persistent CTAs of the weight gradients
   long long step = 0;
   float lr = 1e-3f, b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   Scale4 scale = {{1.f, 1.f, 1.f, 1.f}};
@@ -485,12 +759,11 @@ int forward(lbm_cnn* n, const double* coarse) {
   return LBM_OK;
 }
 
-template <int CIN, int COUT, typename TA>
-void wgrad(lbm_cnn* n, const TA* act, const __nv_bfloat16* dzl, float* grad) {
+template <int CIN, int COUT>
+void wgrad(lbm_cnn* n, const void* act, const __nv_bfloat16* dzl, float* grad) {
   constexpr int NOUT = 9 * CIN * COUT + COUT;
-  const int threads = ru(9 * CIN + COUT, 32);
-  k_wgrad<CIN, COUT, TA><<<n->wblocks, threads, 0, n->stream>>>(act, dzl, n->H, n->W, n->wchunk,
-                                                                 n->wpartial);
+  k_wgrad_tc<CIN, COUT><<<n->wblocks, WG_T, wg_smem<CIN, COUT>(), n->stream>>>(act, dzl, n->H,
+                                                                              n->W, n->wpartial);
   k_sum_partials<<<(NOUT + 255) / 256, 256, 0, n->stream>>>(n->wpartial, n->wblocks, NOUT, grad);
 }
 
@@ -511,7 +784,7 @@ int loss_backward(lbm_cnn* n, const double* target) {
   conv<32, 32, EPI_MASK_BF16>(n, n->dz[0], n->wb[2], nullptr, n->act[2], n->dz[1], nullptr);
   wgrad<32, 32>(n, n->act[1], n->dz[1], g + param_offset(1));
   conv<32, 32, EPI_MASK_BF16>(n, n->dz[1], n->wb[1], nullptr, n->act[1], n->dz[0], nullptr);
-  wgrad<4, 32>(n, (const float*)n->xf, n->dz[0], g + param_offset(0));
+  wgrad<4, 32>(n, n->xf, n->dz[0], g + param_offset(0));
   CCK(n, cudaGetLastError());
   return LBM_OK;
 }
@@ -533,8 +806,18 @@ int lbm_cnn_create(int H, int W, void* cuda_stream, lbm_cnn** out) {
   if (cuda_stream) n->stream = (cudaStream_t)cuda_stream;
   else { e = cudaStreamCreate(&n->stream); n->own_stream = true; }
   const size_t P = n->npix;
-  n->wchunk = 1024;
-  n->wblocks = (int)((P + n->wchunk - 1) / n->wchunk);
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto allow = [&](const void* k, size_t bytes) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  allow((const void*)k_wgrad_tc<32, 32>, wg_smem<32, 32>());
+  allow((const void*)k_wgrad_tc<32, 4>, wg_smem<32, 4>());
+  allow((const void*)k_wgrad_tc<4, 32>, wg_smem<4, 32>());
+  n->wblocks = (int)std::min<long long>((P + WG_CHUNK - 1) / WG_CHUNK,
+                                        (long long)WG_CTAS_PER_SM * std::max(sms, 1));
   auto A = [&](void** p, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes);
     if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, bytes, n->stream);

@@ -226,7 +226,7 @@ struct lbm_ctx {
   bool dwp = false;           // double-word populations and arithmetic (LBM_DF64)
   bool dwmom = false;         // FP32 step, double-word moments (LBM_FP32_DWMOM)
   unsigned char* tc_b = nullptr;  // TF32 parts of M and M^-1 (4 KB)
-  float* tc_w = nullptr;          // -dt s_k, 0 for the conserved k
+  TcWeights tc_w = {};           // -dt s_k, 0 for the conserved k
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int fuse = 1;                   // time steps per FP32 launch (1 or 2)
   CUtensorMap tmap2[2];           // two-step kernel: tile + two-row halo
@@ -603,11 +603,9 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
     float w[16];
     for (int k = 0; k < 16; ++k) w[k] = k < 4 ? 0.f : (float)(-C.dt * C.s[k]);
     e = cudaMalloc((void**)&c->tc_b, sizeof(bconst));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->tc_w, sizeof(w));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(c->tc_b, bconst, sizeof(bconst), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->tc_w, w, sizeof(w), cudaMemcpyHostToDevice, c->stream);
+    memcpy(c->tc_w.w, w, sizeof(w));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   }
   for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(c->f[b], 0, fbytes, c->stream);
@@ -777,7 +775,6 @@ int lbm_destroy(lbm_ctx* c) {
   if (c->staging) cudaFree(c->staging);
   if (c->pstage) cudaFree(c->pstage);
   if (c->tc_b) cudaFree(c->tc_b);
-  if (c->tc_w) cudaFree(c->tc_w);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return LBM_OK;

@@ -1,43 +1,58 @@
 // lbm_tc.cu -- the fused step with the two 16 x 16 moment transforms on the
-// 5th-generation tensor cores (tcgen05.mma, TMEM accumulators), precision
-// LBM_TC_TF32X3 of include/lbm.h.
+// 5th-generation tensor cores (tcgen05.mma, TMEM operands and accumulators),
+// precision LBM_TC_TF32X3 of include/lbm.h.
 //
 // Persistent CTAs of 128 threads (4 warps, TC_CTAS_PER_SM per SM), each taking
-// node tiles b, b + G, b + 2G, ... (G CTAs); a tile is 32 x 4 = 128 nodes,
-// node t of the tile is row t of the MMA and lane t of tensor memory. Once
-// per CTA: 32 TMEM columns are allocated, the transform constants copied to
-// shared memory and the first tile's copy started. Per tile:
+// node tiles b, b + G, b + 2G, ... (G CTAs). A tile is 32 x 8 = 256 nodes;
+// thread t = (tx, ty) holds two of them, rows ty and ty + 4 (nodes a and b),
+// and computes both in paired f32x2 instructions, as the FP32 step does.
+// Node a of thread t is row t of the first set of MMAs, node b row t of the
+// second, so that both live in lane t of tensor memory. Once per CTA: 128
+// TMEM columns are allocated, the transform constants copied to shared
+// memory and the first tile's copy started. TMEM columns:
+//   [0, 16) A high part of node a, [16, 32) its low part,
+//   [32, 48), [48, 64) the same for node b,
+//   [64, 80) D of node a, [80, 96) D of node b.
+// Per tile:
 //   0. TMA: the next tile and its halo into the other shared-memory stage
 //      (double buffering: the copy runs under this tile's work);
 //   1. wait for this tile's copy;
-//   2. A = f (128 x 16) split into TF32 high and low parts (round to nearest,
-//      ties away, by integer rounding of the bit pattern), written to shared
-//      memory in the canonical K-major layout without swizzle;
-//   3. m = f M^T: three products A_hi B_hi + A_hi B_lo + A_lo B_hi (the
-//      3xTF32 split, error ~ the FP32 one), each two K = 8 MMAs issued by one
-//      thread into TMEM columns 0..15 (FP32 accumulation); tcgen05.ld gives
-//      every thread the 16 moments of its node;
-//   4. Eq. 14 equilibria and the relaxation of Eq. 3 on the CUDA cores:
-//      dm_k = -dt s_k (m_k - m_k^eq);
-//   5. df = dm (M^-1)^T, the same split, into TMEM columns 16..31; ld;
-//   6. Lax-Wendroff update with the tile's neighbours, ghosts at the domain
-//      edge, store; audit partial of the tile on audit steps.
+//   2. A = f split into TF32 high and low parts (high: round to nearest,
+//      ties away, by integer rounding of the bit pattern; low = f - high,
+//      exact, whose 13 low bits the TF32 product ignores), written by each
+//      thread into its own TMEM lane (tcgen05.st);
+//   3. m = f M^T: three products A_hi B_hi + A_hi B_lo + A_lo B_hi per node
+//      set (the 3xTF32 split), each two K = 8 MMAs with A from TMEM and B
+//      from shared memory, issued by one thread; FP32 accumulation in TMEM;
+//      tcgen05.ld gives every thread the 16 moments of its two nodes;
+//   4. Eq. 14 equilibria and the relaxation of Eq. 3 on the CUDA cores
+//      (paired): dm_k = -dt s_k (m_k - m_k^eq);
+//   5. df = dm (M^-1)^T, the same split and products; ld;
+//   6. Lax-Wendroff update with the tile's neighbours (paired for interior
+//      pairs), ghosts at the domain edge, store; audit partial of the tile
+//      on audit steps.
 // Watchdog and audit epilogue once per CTA. Every wait (TMA, MMA completion)
 // is bounded in time; on expiry the kernel records LBM_ERR_TIMEOUT, waits
 // once more for the copies and products it issued (bounded), frees its
 // tensor memory and returns.
 #include "lbm_step.cuh"
+#include "tc05.cuh"
 
 #include <cstring>
 
 namespace lbmk {
 namespace {
 
-constexpr int TC_N = TC_X * TC_Y;   // 128 nodes per CTA
+constexpr int TC_HY = TC_Y / 2;                      // node b is TC_HY rows below node a
+constexpr int TC_T = TC_X * TC_HY;                   // 128 threads
 constexpr int TC_BXP = TC_X + 2 * HALO_X, TC_ROWS = TC_Y + 2;
 constexpr int TC_TILE = 16 * TC_ROWS * TC_BXP;
 constexpr unsigned TC_TILE_BYTES = TC_TILE * 4;
-constexpr unsigned TC_TMEM_COLS = 32;
+constexpr unsigned TC_TMEM_COLS = 128;
+constexpr unsigned TM_A = 0, TM_D = 64;              // column bases (see above)
+static_assert(TC_T == 128, "one MMA row per thread");
+static_assert(TC_T / 4 * 4 * sizeof(double) <= TC_TILE * sizeof(float),
+              "the final audit sum's scratch fits one stage");
 
 // Byte offset of element (row, k) of a rows x 16 TF32 operand in the
 // canonical K-major, no-swizzle layout: core matrices of 8 rows x 4 elements
@@ -48,101 +63,69 @@ __device__ __host__ constexpr unsigned canon(int row, int k) {
 constexpr unsigned CANON_LBO = 128;  // next core matrix along K
 constexpr unsigned CANON_SBO = 512;  // next 8-row group
 
-// Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading-dimension
-// byte offset >> 4 (16-29), stride-dimension byte offset >> 4 (32-45), the
-// fixed value 0b001 at bits 46-48, base offset 0, no swizzle (bits 61-63 = 0).
 __device__ __forceinline__ unsigned long long smem_desc(unsigned addr) {
-  return (unsigned long long)((addr >> 4) & 0x3FFF) |
-         ((unsigned long long)((CANON_LBO >> 4) & 0x3FFF) << 16) |
-         ((unsigned long long)((CANON_SBO >> 4) & 0x3FFF) << 32) | (1ull << 46);
+  return tc05::smem_desc(addr, CANON_LBO, CANON_SBO);
 }
+// kind::tf32, M = 128 nodes, N = 16 moments.
+constexpr unsigned TC_IDESC = tc05::idesc_f32acc(tc05::FMT_TF32, 128, 16);
 
-// Instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
-// (bits 7-9 = 2, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits
-// 17-22, M >> 4 at bits 24-28.
-constexpr unsigned TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) |
-                              ((128u >> 4) << 24);
-
-__device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long a, unsigned long long b,
-                                       unsigned accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void tc_commit(unsigned long long* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_addr(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// 16 consecutive TMEM columns of this warp's 32 lanes (lane = thread).
-__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
-  unsigned r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// Twelve MMAs: for each node set n (a, b), D_n = A_n,hi B_hi + A_n,hi B_lo +
+// A_n,lo B_hi over K = 16 (two K = 8 halves), A from TMEM.
+__device__ __forceinline__ void tc_product(unsigned tmem, unsigned b_hi, unsigned b_lo) {
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Six MMAs: D = A_hi B_hi + A_hi B_lo + A_lo B_hi over K = 16 (two K = 8 halves).
-__device__ __forceinline__ void tc_product(unsigned tmem_d, unsigned a_hi, unsigned a_lo,
-                                           unsigned b_hi, unsigned b_lo) {
-  const unsigned As[3] = {a_hi, a_hi, a_lo}, Bs[3] = {b_hi, b_lo, b_hi};
+  for (int n = 0; n < 2; ++n) {
+    const unsigned a_hi = tmem + TM_A + 32 * n, a_lo = a_hi + 16, d = tmem + TM_D + 16 * n;
+    const unsigned As[3] = {a_hi, a_hi, a_lo}, Bs[3] = {b_hi, b_lo, b_hi};
 #pragma unroll
-  for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-      tc_mma(tmem_d, smem_desc(As[p] + h * 2 * CANON_LBO), smem_desc(Bs[p] + h * 2 * CANON_LBO),
-             (p | h) ? 1u : 0u);
+      for (int h = 0; h < 2; ++h)
+        tc05::mma_tf32_ta(d, As[p] + 8 * h, smem_desc(Bs[p] + h * 2 * CANON_LBO), TC_IDESC,
+                          (p | h) ? 1u : 0u);
+  }
 }
 
 // TF32 rounding of an FP32 value (nearest, ties away from zero: half of the
 // last kept bit added to the magnitude's bit pattern, the 13 low bits
 // cleared): two integer operations instead of a conversion.
-__device__ __forceinline__ float tf32_rna(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+__device__ __forceinline__ unsigned tf32_rna_bits(float x) {
+  return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
-// Writes the TF32 high and low parts of v (16 values of row `row`) into the
-// two operand buffers: hi = tf32(v), lo = tf32(v - hi) (v - hi is exact).
-__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int row,
-                                              const float (&v)[16]) {
+// The TF32 high and low parts of the two nodes' 16 values into this
+// thread's lane of the A columns: hi = tf32(v), lo = v - hi (exact; the
+// product reads its 19 high bits). One node at a time (register pressure).
+__device__ __forceinline__ void put_split(unsigned tmem_lane, const F2 (&v)[16]) {
 #pragma unroll
-  for (int kq = 0; kq < 4; ++kq) {
-    float h[4], l[4];
+  for (int n = 0; n < 2; ++n) {
+    unsigned h[16], l[16];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      h[e] = tf32_rna(v[4 * kq + e]);
-      l[e] = tf32_rna(__fsub_rn(v[4 * kq + e], h[e]));
+    for (int k = 0; k < 16; ++k) {
+      const float x = n ? v[k].v.y : v[k].v.x;
+      h[k] = tf32_rna_bits(x);
+      l[k] = __float_as_uint(__fsub_rn(x, __uint_as_float(h[k])));
     }
-    *reinterpret_cast<float4*>(hi + canon(row, 4 * kq)) = make_float4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<float4*>(lo + canon(row, 4 * kq)) = make_float4(l[0], l[1], l[2], l[3]);
+    tc05::st16(tmem_lane + TM_A + 32 * n, h);
+    tc05::st16(tmem_lane + TM_A + 32 * n + 16, l);
   }
+  tc05::st_wait();
+}
+
+// The 16 values of both nodes from this thread's lane of the D columns.
+__device__ __forceinline__ void get_pair(unsigned tmem_lane, F2 (&out)[16]) {
+  float a[16], b[16];
+  tc05::ld16(tmem_lane + TM_D, a);
+  tc05::ld16(tmem_lane + TM_D + 16, b);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) out[k] = F2(a[k], b[k]);
 }
 
 struct TcSmem {
   float tile[2][TC_TILE];                      // two stages: populations + halo (TMA)
-  alignas(128) unsigned char a_hi[TC_N * 64];  // 128 x 16 TF32, canonical layout
-  alignas(128) unsigned char a_lo[TC_N * 64];
   alignas(128) unsigned char b[4][16 * 64];    // M hi, M lo, M^-1 hi, M^-1 lo (16 x 16)
   unsigned long long bar_tma[2], bar_mma;
   unsigned tmem_base;
-  double red[TC_N / 4][4];
+  double red[TC_Y][4];                         // audit sums of a tile's rows
   unsigned long long step;
   int audit, last;
 };
@@ -154,22 +137,16 @@ __device__ __forceinline__ void tc_load_tile(float* dst, const CUtensorMap* tmap
   tma_load_tile(dst, tmap, (tile % tiles_x) * TC_X - HALO_X, (tile / tiles_x) * TC_Y - 1, bar);
 }
 
-__global__ void __launch_bounds__(TC_N, TC_CTAS_PER_SM)
+__global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
     k_step_tc(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ fin,
               float* __restrict__ fout, const StepArgs<float> A,
-              const unsigned char* __restrict__ bconst, const float* __restrict__ wk) {
+              const unsigned char* __restrict__ bconst, const TcWeights wk) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
-  const int t = threadIdx.x, warp = t >> 5;
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * TC_X + tx, warp = ty;
   const int G = (int)gridDim.x;
 
-  if (warp == 0) {  // tensor memory: 32 columns for this CTA, for all its tiles
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_addr(&S.tmem_base)),
-                 "r"(TC_TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 0) tc05::alloc(&S.tmem_base, TC_TMEM_COLS);  // for all this CTA's tiles
   if (t == 0) {
     mbar_init(&S.bar_tma[0], 1);
     mbar_init(&S.bar_tma[1], 1);
@@ -178,17 +155,16 @@ __global__ void __launch_bounds__(TC_N, TC_CTAS_PER_SM)
     S.step = read_step(A, &S.audit);
   }
   // transform constants into shared memory (4 KB)
-  for (int i = t; i < 4 * 16 * 64 / 16; i += TC_N)
+  for (int i = t; i < 4 * 16 * 64 / 16; i += TC_T)
     reinterpret_cast<uint4*>(&S.b[0][0])[i] = reinterpret_cast<const uint4*>(bconst)[i];
-  tc_fence_before();
+  tc05::fence_before();
   __syncthreads();
-  tc_fence_after();
+  tc05::fence_after();
   const unsigned tmem = S.tmem_base;
-  const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
+  const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);  // this thread's lane
   const unsigned long long step = S.step;
   const bool audit = S.audit != 0;
   const float tnow = A.dtr * (float)step;
-  const int tx = t & 31, ty = t >> 5;
   constexpr int PS = TC_ROWS * TC_BXP;
   const unsigned P = (unsigned)A.plane, pitch = (unsigned)A.pitch;
 
@@ -208,21 +184,23 @@ __global__ void __launch_bounds__(TC_N, TC_CTAS_PER_SM)
       if (more) wait_next = (1 - s) * 2 + (((k + 1) >> 1) & 1);
       break;
     }
-    const int x = (cur % A.tiles_x) * TC_X + tx, y = (cur / A.tiles_x) * TC_Y + ty;
-    const bool active = x < A.nx && y < A.ny;
-    const float* ctr = S.tile[s] + (ty + 1) * TC_BXP + tx + HALO_X;
-    float f[16];
+    const int x = (cur % A.tiles_x) * TC_X + tx;
+    const int ya = (cur / A.tiles_x) * TC_Y + ty, yb = ya + TC_HY;
+    const bool act_a = x < A.nx && ya < A.ny, act_b = x < A.nx && yb < A.ny;  // act_b => act_a
+    const float* sa = S.tile[s] + (ty + 1) * TC_BXP + tx + HALO_X;
+    const float* sb = sa + TC_HY * TC_BXP;
+    F2 f[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) f[i] = ctr[i * PS];
+    for (int i = 0; i < 16; ++i) f[i] = F2(sa[i * PS], sb[i * PS]);
 
     // m = f M^T on the tensor cores
-    put_split(S.a_hi, S.a_lo, t, f);
-    fence_async_smem();
+    put_split(trow, f);
+    tc05::fence_before();
     __syncthreads();
     if (t == 0) {
-      tc_fence_after();
-      tc_product(tmem, smem_addr(S.a_hi), smem_addr(S.a_lo), smem_addr(S.b[0]), smem_addr(S.b[1]));
-      tc_commit(&S.bar_mma);
+      tc05::fence_after();
+      tc_product(tmem, smem_addr(S.b[0]), smem_addr(S.b[1]));
+      tc05::commit(&S.bar_mma);
     }
     if (!__syncthreads_and(mbar_wait_bounded(&S.bar_mma, mma_done & 1, TMA_WAIT_CYCLES))) {
       failed = 1;
@@ -231,30 +209,27 @@ __global__ void __launch_bounds__(TC_N, TC_CTAS_PER_SM)
       break;
     }
     ++mma_done;
-    tc_fence_after();
-    float m[16];
-    tc_ld16(trow, m);
+    tc05::fence_after();
+    F2 m[16];
+    get_pair(trow, m);
 
-    // equilibria and relaxation on the CUDA cores
-    Cons<float> c;
-    c.rho = m[0]; c.jx = m[1]; c.jy = m[2]; c.e = m[3];
-    const Eq<float> q = equilibria(c.rho, c.jx, c.jy, c.e);
+    // equilibria and relaxation on the CUDA cores (the A columns are free:
+    // the products that read them have completed)
+    const Eq<F2> q = equilibria(m[0], m[1], m[2], m[3]);
     {
-      const float meq[16] = {m[0], m[1], m[2], m[3], q.m5, q.m6, q.m7, q.m8, q.m9, q.m10,
-                             q.m11, 0.f, q.m13, q.m14, 0.f, 0.f};
-      float dm[16];
+      F2 dm[16];
+      const F2 meq[16] = {m[0], m[1], m[2], m[3], q.m5, q.m6, q.m7, q.m8, q.m9, q.m10,
+                          q.m11, F2(0.0), q.m13, q.m14, F2(0.0), F2(0.0)};
 #pragma unroll
-      for (int kk = 0; kk < 16; ++kk) dm[kk] = wk[kk] * (m[kk] - meq[kk]);
-      tc_fence_before();  // the tcgen05.ld above completes before A is rewritten
-      put_split(S.a_hi, S.a_lo, t, dm);
-      fence_async_smem();
+      for (int kk = 0; kk < 16; ++kk) dm[kk] = wk.w[kk] * (m[kk] - meq[kk]);
+      put_split(trow, dm);
     }
+    tc05::fence_before();
     __syncthreads();
     if (t == 0) {
-      tc_fence_after();
-      tc_product(tmem + 16, smem_addr(S.a_hi), smem_addr(S.a_lo), smem_addr(S.b[2]),
-                 smem_addr(S.b[3]));
-      tc_commit(&S.bar_mma);
+      tc05::fence_after();
+      tc_product(tmem, smem_addr(S.b[2]), smem_addr(S.b[3]));
+      tc05::commit(&S.bar_mma);
     }
     if (!__syncthreads_and(mbar_wait_bounded(&S.bar_mma, mma_done & 1, TMA_WAIT_CYCLES))) {
       failed = 1;
@@ -263,31 +238,69 @@ __global__ void __launch_bounds__(TC_N, TC_CTAS_PER_SM)
       break;
     }
     ++mma_done;
-    tc_fence_after();
-    float df[16];
-    tc_ld16(trow + 16, df);
+    tc05::fence_after();
+    F2 acc[16];
+    get_pair(trow, acc);
 
-    float cons[4] = {0.f, 0.f, 0.f, 0.f};
-    if (active) {
-      const unsigned cidx = (unsigned)y * pitch + (unsigned)x;
-      float acc[16];
+    float mca[4] = {0.f, 0.f, 0.f, 0.f}, mcb[4] = {0.f, 0.f, 0.f, 0.f};
+    if (act_a) {
+      const unsigned ca = (unsigned)ya * pitch + (unsigned)x, cb = ca + TC_HY * pitch;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) acc[i] = A.K.a0[i] * f[i] + df[i];
-      const bool b = !(c.rho > 0.f) ||
-                     ((__float_as_uint(c.rho + c.jx + c.jy + c.e) & 0x7f800000u) == 0x7f800000u);
-      bad |= b;
-      negT |= !b && !(q.P > 0.f);
-      cons[0] = c.rho; cons[1] = c.jx; cons[2] = c.jy; cons[3] = c.e;
-      neighbour_terms<float, unsigned, TC_BXP>(A, fin, ctr, PS, P, pitch, cidx, x, y, c, tnow, acc);
+      for (int i = 0; i < 16; ++i) acc[i] = A.K.a0[i] * f[i] + acc[i];
+      const bool ba = !(m[0].v.x > 0.f) || !isfinite(m[0].v.x + m[1].v.x + m[2].v.x + m[3].v.x);
+      const bool bb = act_b && (!(m[0].v.y > 0.f) || !isfinite(m[0].v.y + m[1].v.y + m[2].v.y + m[3].v.y));
+      bad |= ba || bb;
+      negT |= (!ba && !(q.P.v.x > 0.f)) || (act_b && !bb && !(q.P.v.y > 0.f));
 #pragma unroll
-      for (int i = 0; i < 16; ++i) fout[i * P + cidx] = acc[i];
+      for (int c = 0; c < 4; ++c) mca[c] = m[c].v.x;
+      if (act_b)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) mcb[c] = m[c].v.y;
+
+      if (act_b && x > 0 && x < A.nx - 1 && ya > 0 && yb < A.ny - 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          F2 a = acc[i];
+          if (has_x(i)) {
+            a = A.K.aW[i] * F2(sa[i * PS - 1], sb[i * PS - 1]) + a;
+            a = A.K.aE[i] * F2(sa[i * PS + 1], sb[i * PS + 1]) + a;
+          }
+          if (has_y(i)) {
+            a = A.K.aS[i] * F2(sa[i * PS - TC_BXP], sb[i * PS - TC_BXP]) + a;
+            a = A.K.aN[i] * F2(sa[i * PS + TC_BXP], sb[i * PS + TC_BXP]) + a;
+          }
+          fout[i * P + ca] = a.v.x;
+          fout[i * P + cb] = a.v.y;
+        }
+      } else {
+        float acc1[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc1[i] = acc[i].v.x;
+        const Cons<float> m1 = {m[0].v.x, m[1].v.x, m[2].v.x, m[3].v.x};
+        neighbour_terms<float, unsigned, TC_BXP>(A, fin, sa, PS, P, pitch, ca, x, ya, m1, tnow, acc1);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) fout[i * P + ca] = acc1[i];
+        if (act_b) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc1[i] = acc[i].v.y;
+          const Cons<float> m2 = {m[0].v.y, m[1].v.y, m[2].v.y, m[3].v.y};
+          neighbour_terms<float, unsigned, TC_BXP>(A, fin, sb, PS, P, pitch, cb, x, yb, m2, tnow, acc1);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) fout[i * P + cb] = acc1[i];
+        }
+      }
     }
     if (audit) {  // per-tile partial (fixed order whatever the CTA)
-      const double v[4] = {widen(cons[0]), widen(cons[1]), widen(cons[2]), widen(cons[3])};
-      audit_tile<TC_N>(A, cur, v, S.red);
+      double va[4], vb[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        va[c] = widen(mca[c]);
+        vb[c] = widen(mcb[c]);
+      }
+      audit_pair_rows<TC_X, TC_Y>(A, cur, va, vb, S.red);
     }
-    // stage s, the operand buffers and TMEM are free for the next tile
-    tc_fence_before();
+    // stage s and TMEM are free for the next tile
+    tc05::fence_before();
     __syncthreads();
   }
 
@@ -301,25 +314,21 @@ __global__ void __launch_bounds__(TC_N, TC_CTAS_PER_SM)
       if (wait_mma) mbar_wait_bounded(&S.bar_mma, mma_done & 1, TMA_WAIT_CYCLES);
       audit_ticket_on_exit(A, audit);
     }
-    tc_fence_before();
+    tc05::fence_before();
     __syncthreads();
-    if (warp == 0)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                   "r"(TC_TMEM_COLS)
-                   : "memory");
+    if (warp == 0) tc05::dealloc(tmem, TC_TMEM_COLS);
     return;
   }
 
   // free tensor memory (every tcgen05.ld of this CTA is complete)
-  tc_fence_before();
+  tc05::fence_before();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TC_TMEM_COLS)
-                 : "memory");
+  if (warp == 0) tc05::dealloc(tmem, TC_TMEM_COLS);
 
   watchdog_flags(A.st, step, bad, negT);
-  if (audit) audit_finish<TC_N>(A, step, S.red, &S.last);
+  // the final sum's scratch (N / 4 rows) in stage 0, free now: no copy is
+  // in flight and every thread has passed its last tile
+  if (audit) audit_finish<TC_T>(A, step, reinterpret_cast<double(*)[4]>(S.tile[0]), &S.last);
 }
 
 }  // namespace
@@ -366,9 +375,9 @@ cudaError_t tc_prepare() {
 }
 
 cudaError_t tc_launch(const CUtensorMap& tm, const float* fin, float* fout,
-                      const StepArgs<float>& A, const unsigned char* bconst, const float* wk,
+                      const StepArgs<float>& A, const unsigned char* bconst, const TcWeights& wk,
                       dim3 grid, cudaStream_t s) {
-  k_step_tc<<<grid, TC_N, sizeof(TcSmem), s>>>(tm, fin, fout, A, bconst, wk);
+  k_step_tc<<<grid, dim3(TC_X, TC_HY), sizeof(TcSmem), s>>>(tm, fin, fout, A, bconst, wk);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,124 @@
+// tc05.cuh -- 5th-generation tensor-core primitives (tcgen05) in inline PTX,
+// shared by the tensor-core step (lbm_tc.cu) and the corrector's weight
+// gradients (lbm_cnn.cu): tensor-memory allocation, shared-memory matrix and
+// instruction descriptors, MMA issue and completion, loads from tensor
+// memory. One elected thread issues MMAs; completion is signalled on an
+// mbarrier by tcgen05.commit; every wait on it is bounded by the caller.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tma.cuh"
+
+namespace tc05 {
+
+using gbtma::smem_addr;
+
+// Shared-memory matrix descriptor of an operand in the canonical K-major
+// layout without swizzle (core matrices of 8 rows x 16 bytes, 128 contiguous
+// bytes): start >> 4 (bits 0-13), leading-dimension byte offset >> 4 (the
+// next core matrix along K; bits 16-29), stride-dimension byte offset >> 4
+// (the next 8-row group; bits 32-45), the fixed value 0b001 at bits 46-48,
+// base offset 0, no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr >> 4) & 0x3FFF) |
+         ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor with an FP32 accumulator (bits 4-5 = 1), A and B of
+// format `fmt` (bits 7-9, 10-12: kind::f16 0 = F16, 1 = BF16; kind::tf32 2 =
+// TF32), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits
+// 24-28.
+__host__ __device__ constexpr unsigned idesc_f32acc(unsigned fmt, unsigned M, unsigned N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+constexpr unsigned FMT_BF16 = 1, FMT_TF32 = 2;
+
+__device__ __forceinline__ void mma_tf32(unsigned tmem_d, unsigned long long a, unsigned long long b,
+                                         unsigned idesc, unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_f16(unsigned tmem_d, unsigned long long a, unsigned long long b,
+                                        unsigned idesc, unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// The same with A in tensor memory: row m of A in lane m, its K = 8 TF32
+// elements in 8 consecutive columns from `tmem_a`.
+__device__ __forceinline__ void mma_tf32_ta(unsigned tmem_d, unsigned tmem_a, unsigned long long b,
+                                            unsigned idesc, unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrives on `bar` once every MMA issued before by this thread has completed.
+__device__ __forceinline__ void commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Orders this thread's shared-memory writes with later reads by the tensor
+// cores (the async proxy).
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Warp-wide: `ncols` (a power of two >= 32) tensor-memory columns; the base
+// address is written to `*dst` in shared memory. Then gives up the
+// allocation permit so that other CTAs on the SM can allocate.
+__device__ __forceinline__ void alloc(unsigned* dst, unsigned ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_addr(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+// Warp-wide: frees what alloc gave.
+__device__ __forceinline__ void dealloc(unsigned taddr, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// 16 consecutive TMEM columns of this warp's 32 lanes (lane = thread).
+__device__ __forceinline__ void ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 values into 16 consecutive TMEM columns of this warp's 32 lanes (lane =
+// thread); complete them with st_wait() before they are used.
+__device__ __forceinline__ void st16(unsigned taddr, const unsigned (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+}  // namespace tc05

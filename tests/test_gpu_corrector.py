@@ -1,8 +1,8 @@
 """GPU tests of the learned coarse-grid corrector (include/lbm_cnn.h).
 
 * Loss and every parameter gradient of the GPU network (an FP32 first layer
-  on the FP32 features, then BF16 tensor-core convolutions with FP32
-  accumulation) against the FP64 CPU reference (oracle/cnn.py) run with the
+  on the FP32 features, then BF16 tensor-core convolutions and weight
+  gradients with FP32 accumulation) against the FP64 CPU reference (oracle/cnn.py) run with the
   same BF16 rounding of the later layers' parameters, the stored activations
   and the stored output gradients:
   what is left is FP32-vs-FP64 accumulation order, so the bar is a relative
@@ -45,12 +45,14 @@ def _fields(rng, H, W):
     return np.stack([rho, u, v, T])
 
 
-@pytest.mark.parametrize("loss_kind", ["mse", "l1"])
-def test_gradients_match_cpu_reference(loss_kind):
+@pytest.mark.parametrize("loss_kind,H,W", [("mse", 13, 11), ("l1", 13, 11), ("mse", 257, 203)])
+def test_gradients_match_cpu_reference(loss_kind, H, W):
+    """13 x 11: three 64-pixel chunks of the tensor-core weight gradients, the
+    last one ragged; 257 x 203: 816 chunks, so that some CTAs of the
+    persistent grid (4 per SM) accumulate two chunks in tensor memory."""
     import torch
     from paper_0908_3749_gb300 import lbm, corrector
     rng = np.random.default_rng(0)
-    H, W = 13, 11
     params = corrector.init_params(3)
     last = _unpack(params)[-1][0]
     last[...] = rng.standard_normal(last.shape) * 0.05      # non-zero last layer

@@ -1,9 +1,11 @@
 """GPU tests of the tensor-core step (precision LBM_TC_TF32X3): the two
-16 x 16 moment transforms run as tcgen05 MMAs over 128-node tiles with the
-3xTF32 split (a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulation).
+16 x 16 moment transforms run as tcgen05 MMAs (A in tensor memory, two nodes
+per thread, 32 x 8 node tiles) with the 3xTF32 split (a_hi b_hi + a_hi b_lo
++ a_lo b_hi, FP32 accumulation).
 
 Bar against the FP64 oracle: the same bound as the FP32 step (the dropped
-a_lo b_lo term is below 2^-22 relative, under FP32 rounding): relative
+a_lo b_lo term and the product's reading of a_lo to 19 bits are each below
+2^-21 relative, a few units of FP32 rounding): relative
 L-infinity <= 30 u sqrt(n) + 3e-6 for smooth flows, u = 2^-24. The audit and
 the watchdog run through the same epilogue as the other precisions.
 """
