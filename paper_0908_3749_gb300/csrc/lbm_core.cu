@@ -225,7 +225,7 @@ struct lbm_ctx {
   bool tc = false;            // tensor-core transforms (LBM_TC_TF32X3)
   bool dwp = false;           // double-word populations and arithmetic (LBM_DF64)
   bool dwmom = false;         // FP32 step, double-word moments (LBM_FP32_DWMOM)
-  unsigned char* tc_b = nullptr;  // TF32 parts of M and M^-1 (4 KB)
+  unsigned char* tc_b = nullptr;  // TF32 parts of M and M^-1 (16 KB)
   TcWeights tc_w = {};           // -dt s_k, 0 for the conserved k
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int fuse = 1;                   // time steps per FP32 launch (1 or 2)
@@ -594,7 +594,7 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
     e = cudaMalloc((void**)&c->staging, sizeof(double) * 4 * (size_t)C.nx * C.ny);
   if (e == cudaSuccess && c->tc) {
     double M[16][16], Minv[16][16];
-    unsigned char bconst[4][1024];
+    unsigned char bconst[4][4096];
     if (!dense_moment_matrices(M, Minv)) {
       lbm_destroy(c);
       return fail(nullptr, LBM_ERR_INVALID, "singular moment matrix");

@@ -6,13 +6,18 @@
 // node tiles b, b + G, b + 2G, ... (G CTAs). A tile is 32 x 8 = 256 nodes;
 // thread t = (tx, ty) holds two of them, rows ty and ty + 4 (nodes a and b),
 // and computes both in paired f32x2 instructions, as the FP32 step does.
-// Node a of thread t is row t of the first set of MMAs, node b row t of the
-// second, so that both live in lane t of tensor memory. Once per CTA: 128
-// TMEM columns are allocated, the transform constants copied to shared
-// memory and the first tile's copy started. TMEM columns:
-//   [0, 16) A high part of node a, [16, 32) its low part,
-//   [32, 48), [48, 64) the same for node b,
-//   [64, 80) D of node a, [80, 96) D of node b.
+// Both nodes of thread t are row t of the MMAs (lane t of tensor memory):
+// the A row holds node a's 16 values in K = 0..15 and node b's in 16..31,
+// and B (32 x 32) maps them to interleaved output columns, 2k for moment k
+// of node a and 2k + 1 for node b, so that one 32-column load gives every
+// thread its pairs ready for the paired arithmetic. (The other node's values
+// enter each output with zero coefficients: a non-finite population of one
+// node makes its partner non-finite in the same step, which the watchdog
+// reports at that step either way.) Once per CTA: 128 TMEM
+// columns are allocated, the transform constants copied to shared memory
+// and the first tile's copy started. TMEM columns:
+//   [0, 32) A high parts (node a, node b), [32, 64) A low parts,
+//   [64, 96) D, interleaved.
 // Per tile:
 //   0. TMA: the next tile and its halo into the other shared-memory stage
 //      (double buffering: the copy runs under this tile's work);
@@ -21,9 +26,9 @@
 //      ties away, by integer rounding of the bit pattern; low = f - high,
 //      exact, whose 13 low bits the TF32 product ignores), written by each
 //      thread into its own TMEM lane (tcgen05.st);
-//   3. m = f M^T: three products A_hi B_hi + A_hi B_lo + A_lo B_hi per node
-//      set (the 3xTF32 split), each two K = 8 MMAs with A from TMEM and B
-//      from shared memory, issued by one thread; FP32 accumulation in TMEM;
+//   3. m = f M^T: three products A_hi B_hi + A_hi B_lo + A_lo B_hi (the
+//      3xTF32 split), each four K = 8 MMAs with A from TMEM and B from
+//      shared memory, issued by one thread; FP32 accumulation in TMEM;
 //      tcgen05.ld gives every thread the 16 moments of its two nodes;
 //   4. Eq. 14 equilibria and the relaxation of Eq. 3 on the CUDA cores
 //      (paired): dm_k = -dt s_k (m_k - m_k^eq);
@@ -49,40 +54,37 @@ constexpr int TC_BXP = TC_X + 2 * HALO_X, TC_ROWS = TC_Y + 2;
 constexpr int TC_TILE = 16 * TC_ROWS * TC_BXP;
 constexpr unsigned TC_TILE_BYTES = TC_TILE * 4;
 constexpr unsigned TC_TMEM_COLS = 128;
-constexpr unsigned TM_A = 0, TM_D = 64;              // column bases (see above)
+constexpr unsigned TM_HI = 0, TM_LO = 32, TM_D = 64;  // column bases (see above)
 static_assert(TC_T == 128, "one MMA row per thread");
 static_assert(TC_T / 4 * 4 * sizeof(double) <= TC_TILE * sizeof(float),
               "the final audit sum's scratch fits one stage");
 
-// Byte offset of element (row, k) of a rows x 16 TF32 operand in the
+// Byte offset of element (row, k) of a rows x 32 TF32 operand in the
 // canonical K-major, no-swizzle layout: core matrices of 8 rows x 4 elements
-// (128 contiguous bytes), 4 core matrices along K per 8-row group.
+// (128 contiguous bytes), 8 core matrices along K per 8-row group.
 __device__ __host__ constexpr unsigned canon(int row, int k) {
-  return (unsigned)((((row >> 3) * 4 + (k >> 2)) * 128) + (row & 7) * 16 + (k & 3) * 4);
+  return (unsigned)((((row >> 3) * 8 + (k >> 2)) * 128) + (row & 7) * 16 + (k & 3) * 4);
 }
-constexpr unsigned CANON_LBO = 128;  // next core matrix along K
-constexpr unsigned CANON_SBO = 512;  // next 8-row group
+constexpr unsigned CANON_LBO = 128;   // next core matrix along K
+constexpr unsigned CANON_SBO = 1024;  // next 8-row group
+constexpr unsigned TC_B_BYTES = 32 * 32 * 4;
 
 __device__ __forceinline__ unsigned long long smem_desc(unsigned addr) {
   return tc05::smem_desc(addr, CANON_LBO, CANON_SBO);
 }
-// kind::tf32, M = 128 nodes, N = 16 moments.
-constexpr unsigned TC_IDESC = tc05::idesc_f32acc(tc05::FMT_TF32, 128, 16);
+// kind::tf32, M = 128 nodes, N = 32 (16 moments x 2 nodes, interleaved).
+constexpr unsigned TC_IDESC = tc05::idesc_f32acc(tc05::FMT_TF32, 128, 32);
 
-// Twelve MMAs: for each node set n (a, b), D_n = A_n,hi B_hi + A_n,hi B_lo +
-// A_n,lo B_hi over K = 16 (two K = 8 halves), A from TMEM.
+// Twelve MMAs: D = A_hi B_hi + A_hi B_lo + A_lo B_hi over K = 32 (four
+// K = 8 slices), A from TMEM.
 __device__ __forceinline__ void tc_product(unsigned tmem, unsigned b_hi, unsigned b_lo) {
+  const unsigned As[3] = {tmem + TM_HI, tmem + TM_HI, tmem + TM_LO}, Bs[3] = {b_hi, b_lo, b_hi};
 #pragma unroll
-  for (int n = 0; n < 2; ++n) {
-    const unsigned a_hi = tmem + TM_A + 32 * n, a_lo = a_hi + 16, d = tmem + TM_D + 16 * n;
-    const unsigned As[3] = {a_hi, a_hi, a_lo}, Bs[3] = {b_hi, b_lo, b_hi};
+  for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        tc05::mma_tf32_ta(d, As[p] + 8 * h, smem_desc(Bs[p] + h * 2 * CANON_LBO), TC_IDESC,
-                          (p | h) ? 1u : 0u);
-  }
+    for (int q = 0; q < 4; ++q)
+      tc05::mma_tf32_ta(tmem + TM_D, As[p] + 8 * q, smem_desc(Bs[p] + q * 2 * CANON_LBO), TC_IDESC,
+                        (p | q) ? 1u : 0u);
 }
 
 // TF32 rounding of an FP32 value (nearest, ties away from zero: half of the
@@ -94,7 +96,7 @@ __device__ __forceinline__ unsigned tf32_rna_bits(float x) {
 
 // The TF32 high and low parts of the two nodes' 16 values into this
 // thread's lane of the A columns: hi = tf32(v), lo = v - hi (exact; the
-// product reads its 19 high bits). One node at a time (register pressure).
+// product reads its 19 high bits).
 __device__ __forceinline__ void put_split(unsigned tmem_lane, const F2 (&v)[16]) {
 #pragma unroll
   for (int n = 0; n < 2; ++n) {
@@ -105,24 +107,23 @@ __device__ __forceinline__ void put_split(unsigned tmem_lane, const F2 (&v)[16])
       h[k] = tf32_rna_bits(x);
       l[k] = __float_as_uint(__fsub_rn(x, __uint_as_float(h[k])));
     }
-    tc05::st16(tmem_lane + TM_A + 32 * n, h);
-    tc05::st16(tmem_lane + TM_A + 32 * n + 16, l);
+    tc05::st16(tmem_lane + TM_HI + 16 * n, h);
+    tc05::st16(tmem_lane + TM_LO + 16 * n, l);
   }
   tc05::st_wait();
 }
 
-// The 16 values of both nodes from this thread's lane of the D columns.
+// The 16 values of both nodes, as pairs, from this thread's lane of D.
 __device__ __forceinline__ void get_pair(unsigned tmem_lane, F2 (&out)[16]) {
-  float a[16], b[16];
-  tc05::ld16(tmem_lane + TM_D, a);
-  tc05::ld16(tmem_lane + TM_D + 16, b);
+  float r[32];
+  tc05::ld32(tmem_lane + TM_D, r);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) out[k] = F2(a[k], b[k]);
+  for (int k = 0; k < 16; ++k) out[k] = F2(r[2 * k], r[2 * k + 1]);
 }
 
 struct TcSmem {
   float tile[2][TC_TILE];                      // two stages: populations + halo (TMA)
-  alignas(128) unsigned char b[4][16 * 64];    // M hi, M lo, M^-1 hi, M^-1 lo (16 x 16)
+  alignas(128) unsigned char b[4][TC_B_BYTES];  // M hi, M lo, M^-1 hi, M^-1 lo (32 x 32)
   unsigned long long bar_tma[2], bar_mma;
   unsigned tmem_base;
   double red[TC_Y][4];                         // audit sums of a tile's rows
@@ -154,8 +155,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
     tc_load_tile(S.tile[0], &tmap, &S.bar_tma[0], blockIdx.x, A.tiles_x);  // grid <= ntiles
     S.step = read_step(A, &S.audit);
   }
-  // transform constants into shared memory (4 KB)
-  for (int i = t; i < 4 * 16 * 64 / 16; i += TC_T)
+  // transform constants into shared memory (16 KB)
+  for (int i = t; i < 4 * (int)TC_B_BYTES / 16; i += TC_T)
     reinterpret_cast<uint4*>(&S.b[0][0])[i] = reinterpret_cast<const uint4*>(bconst)[i];
   tc05::fence_before();
   __syncthreads();
@@ -214,7 +215,11 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
     get_pair(trow, m);
 
     // equilibria and relaxation on the CUDA cores (the A columns are free:
-    // the products that read them have completed)
+    // the products that read them have completed). A node outside the grid
+    // (zeros from the copy) gets density 1, so that its relaxation stays
+    // finite: its partner's products multiply it by zero coefficients.
+    if (!act_a) m[0].v.x = 1.f;
+    if (!act_b) m[0].v.y = 1.f;
     const Eq<F2> q = equilibria(m[0], m[1], m[2], m[3]);
     {
       F2 dm[16];
@@ -347,23 +352,27 @@ float tf32_host(float x) {  // round to nearest (ties away), 10 mantissa bits ke
 
 }  // namespace
 
-// Canonical-layout TF32 hi/lo parts of M and M^-1 as the K-major B operands
-// (row n of B^T = row n of M for m = f M^T; row p of M^-1 for df = dm M^-T),
-// 4 x 1 KB, and the relaxation weights w_k = -dt s_k (0 for k < 4).
+// Canonical-layout TF32 hi/lo parts of the 32 x 32 B operands of M and
+// M^-1, 4 x 4 KB. Row n of B^T (output column n = 2k + node) takes K index
+// node * 16 + j (population or moment j of that node): the entry of row k,
+// column j of M (m = f M^T) or of M^-1 (df = dm M^-T); zero for the other
+// node. Relaxation weights w_k = -dt s_k are applied on the CUDA cores.
 void tc_prepare_constants(const double (&M)[16][16], const double (&Minv)[16][16],
-                          unsigned char (&out)[4][1024]) {
+                          unsigned char (&out)[4][4096]) {
   memset(out, 0, sizeof(out));
-  for (int n = 0; n < 16; ++n)
-    for (int k = 0; k < 16; ++k) {
-      const float vm = (float)M[n][k], vi = (float)Minv[n][k];
+  for (int k = 0; k < 16; ++k)
+    for (int j = 0; j < 16; ++j) {
+      const float vm = (float)M[k][j], vi = (float)Minv[k][j];
       const float mh = tf32_host(vm), ih = tf32_host(vi);
-      const float ml = tf32_host((float)(M[n][k] - (double)mh));
-      const float il = tf32_host((float)(Minv[n][k] - (double)ih));
-      const unsigned off = canon(n, k);
-      memcpy(out[0] + off, &mh, 4);
-      memcpy(out[1] + off, &ml, 4);
-      memcpy(out[2] + off, &ih, 4);
-      memcpy(out[3] + off, &il, 4);
+      const float ml = tf32_host((float)(M[k][j] - (double)mh));
+      const float il = tf32_host((float)(Minv[k][j] - (double)ih));
+      for (int node = 0; node < 2; ++node) {
+        const unsigned off = canon(2 * k + node, 16 * node + j);
+        memcpy(out[0] + off, &mh, 4);
+        memcpy(out[1] + off, &ml, 4);
+        memcpy(out[2] + off, &ih, 4);
+        memcpy(out[3] + off, &il, 4);
+      }
     }
 }
 
