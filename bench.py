@@ -465,7 +465,8 @@ def traffic_record(kernel):
 # The sources that define the one-step grid kernels (their DRAM counts in
 # profiles/traffic.json are valid while these files are unchanged; host code
 # that launches them is not among them).
-STEP_SOURCES = ("lbm_step_kernels.cuh", "lbm_step.cuh", "d2v16.cuh", "tma.cuh", "coeffs.h")
+STEP_SOURCES = ("lbm_step_kernels.cuh", "lbm_step.cuh", "d2v16.cuh", "tma.cuh", "coeffs.h",
+                "dw.cuh", "lbm_dw_step.cuh")
 
 
 def source_hash():

@@ -460,7 +460,10 @@ __device__ __forceinline__ void audit_pair_rows(const StepArgs<R>& A, int cur, c
 // Tensor-core step (lbm_tc.cu)
 // ---------------------------------------------------------------------------
 constexpr int TC_X = 32, TC_Y = 8;  // nodes per tile: 32 x 8 = 256 (two per thread)
-constexpr int TC_CTAS_PER_SM = 3;   // persistent CTAs per SM (shared memory)
+#ifndef LBM_TC_CTAS_PER_SM
+#define LBM_TC_CTAS_PER_SM 3
+#endif
+constexpr int TC_CTAS_PER_SM = LBM_TC_CTAS_PER_SM;  // persistent CTAs per SM
 cudaError_t tc_prepare();           // shared-memory attribute of the kernel
 // TF32 high/low parts of M and M^-1 in the layout the kernel stages (4 x 4 KB).
 void tc_prepare_constants(const double (&M)[16][16], const double (&Minv)[16][16],

@@ -13,14 +13,15 @@
 // thread its pairs ready for the paired arithmetic. (The other node's values
 // enter each output with zero coefficients: a non-finite population of one
 // node makes its partner non-finite in the same step, which the watchdog
-// reports at that step either way.) Once per CTA: 128 TMEM
-// columns are allocated, the transform constants copied to shared memory
-// and the first tile's copy started. TMEM columns:
+// reports at that step either way.) Once per CTA: 128 TMEM columns are
+// allocated, the transform constants copied to shared memory and the first
+// tile's copy started. TMEM columns:
 //   [0, 32) A high parts (node a, node b), [32, 64) A low parts,
 //   [64, 96) D, interleaved.
 // Per tile:
-//   0. TMA: the next tile and its halo into the other shared-memory stage
-//      (double buffering: the copy runs under this tile's work);
+//   0. TMA: the next tile and its halo (two stages: into the other stage at
+//      the start, so that the copy runs under this tile's work; one stage:
+//      at the end, the other CTAs on the SM working meanwhile);
 //   1. wait for this tile's copy;
 //   2. A = f split into TF32 high and low parts (high: round to nearest,
 //      ties away, by integer rounding of the bit pattern; low = f - high,
@@ -54,6 +55,16 @@ constexpr int TC_BXP = TC_X + 2 * HALO_X, TC_ROWS = TC_Y + 2;
 constexpr int TC_TILE = 16 * TC_ROWS * TC_BXP;
 constexpr unsigned TC_TILE_BYTES = TC_TILE * 4;
 constexpr unsigned TC_TMEM_COLS = 128;
+// Shared-memory stages of the tile copy: 2 (the default, with 3 CTAs per SM)
+// overlaps the next tile's copy with this tile's work inside the CTA; 1
+// leaves room (and tensor memory) for TC_CTAS_PER_SM = 4 CTAs, which overlap
+// one another's copies instead. Measured on 2048 x 1024: 0.072 against
+// 0.089 ms per step.
+#ifndef LBM_TC_STAGES
+#define LBM_TC_STAGES 2
+#endif
+constexpr int TC_STAGES = LBM_TC_STAGES;
+static_assert(TC_STAGES == 1 || TC_STAGES == 2, "one or two stages");
 constexpr unsigned TM_HI = 0, TM_LO = 32, TM_D = 64;  // column bases (see above)
 static_assert(TC_T == 128, "one MMA row per thread");
 static_assert(TC_T / 4 * 4 * sizeof(double) <= TC_TILE * sizeof(float),
@@ -122,9 +133,9 @@ __device__ __forceinline__ void get_pair(unsigned tmem_lane, F2 (&out)[16]) {
 }
 
 struct TcSmem {
-  float tile[2][TC_TILE];                      // two stages: populations + halo (TMA)
+  float tile[TC_STAGES][TC_TILE];              // populations + halo (TMA)
   alignas(128) unsigned char b[4][TC_B_BYTES];  // M hi, M lo, M^-1 hi, M^-1 lo (32 x 32)
-  unsigned long long bar_tma[2], bar_mma;
+  unsigned long long bar_tma[TC_STAGES], bar_mma;
   unsigned tmem_base;
   double red[TC_Y][4];                         // audit sums of a tile's rows
   unsigned long long step;
@@ -149,8 +160,7 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
 
   if (warp == 0) tc05::alloc(&S.tmem_base, TC_TMEM_COLS);  // for all this CTA's tiles
   if (t == 0) {
-    mbar_init(&S.bar_tma[0], 1);
-    mbar_init(&S.bar_tma[1], 1);
+    for (int i = 0; i < TC_STAGES; ++i) mbar_init(&S.bar_tma[i], 1);
     mbar_init(&S.bar_mma, 1);
     tc_load_tile(S.tile[0], &tmap, &S.bar_tma[0], blockIdx.x, A.tiles_x);  // grid <= ntiles
     S.step = read_step(A, &S.audit);
@@ -175,14 +185,16 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
   int failed = 0, wait_tma = -1, wait_next = -1, wait_mma = 0;
   int k = 0;
   for (int cur = blockIdx.x; cur < A.ntiles; cur += G, ++k) {
-    const int s = k & 1;
+    const int s = k % TC_STAGES, ph = (k / TC_STAGES) & 1;
+    const int next_wait = TC_STAGES == 2 && cur + G < A.ntiles ? (1 - s) * 2 + (((k + 1) >> 1) & 1) : -1;
     const bool more = cur + G < A.ntiles;
-    // Stage 1 - s was released at the end of the previous tile.
-    if (t == 0 && more) tc_load_tile(S.tile[1 - s], &tmap, &S.bar_tma[1 - s], cur + G, A.tiles_x);
-    if (!__syncthreads_and(mbar_wait_bounded(&S.bar_tma[s], (k >> 1) & 1, TMA_WAIT_CYCLES))) {
+    // Two stages: stage 1 - s was released at the end of the previous tile.
+    if (TC_STAGES == 2 && t == 0 && more)
+      tc_load_tile(S.tile[1 - s], &tmap, &S.bar_tma[1 - s], cur + G, A.tiles_x);
+    if (!__syncthreads_and(mbar_wait_bounded(&S.bar_tma[s], ph, TMA_WAIT_CYCLES))) {
       failed = 1;
-      wait_tma = s * 2 + ((k >> 1) & 1);
-      if (more) wait_next = (1 - s) * 2 + (((k + 1) >> 1) & 1);
+      wait_tma = s * 2 + ph;
+      wait_next = next_wait;
       break;
     }
     const int x = (cur % A.tiles_x) * TC_X + tx;
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
     if (!__syncthreads_and(mbar_wait_bounded(&S.bar_mma, mma_done & 1, TMA_WAIT_CYCLES))) {
       failed = 1;
       wait_mma = 1;
-      if (more) wait_next = (1 - s) * 2 + (((k + 1) >> 1) & 1);
+      wait_next = next_wait;
       break;
     }
     ++mma_done;
@@ -239,7 +251,7 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
     if (!__syncthreads_and(mbar_wait_bounded(&S.bar_mma, mma_done & 1, TMA_WAIT_CYCLES))) {
       failed = 1;
       wait_mma = 1;
-      if (more) wait_next = (1 - s) * 2 + (((k + 1) >> 1) & 1);
+      wait_next = next_wait;
       break;
     }
     ++mma_done;
@@ -307,6 +319,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
     // stage s and TMEM are free for the next tile
     tc05::fence_before();
     __syncthreads();
+    if (TC_STAGES == 1 && t == 0 && more)
+      tc_load_tile(S.tile[0], &tmap, &S.bar_tma[0], cur + G, A.tiles_x);
   }
 
   if (failed) {
