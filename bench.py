@@ -675,10 +675,14 @@ def run_ours(args):
         pass
     hbm_peak = peaks_file.get("hbm_gbs", 6800.0)
 
-    # Headline: FP64 step on the 2048 x 1024 grid. The launch shape is
-    # autotuned first (timed launches that leave the state untouched).
-    ctx = make_ctx(lbm, w, "fp64", args.audit_every, stream)
+    # Headline: FP64 step on the 2048 x 1024 grid, one block per 32 x 2 node
+    # tile (k_step<double>; the autotuner's persistent candidates measure
+    # within 0.1 % of it here, so the timed kernel is fixed, the one whose
+    # DRAM counters profiles/traffic.json holds).
+    ctx = make_ctx(lbm, w, "fp64", args.audit_every, stream, tune=False)
     blocks = lbm.lbm_step_blocks(ctx)
+    tiles = -(-w.nx // 32) * -(-w.ny // 2)
+    kname = "k_step<double>" if blocks >= tiles else "k_step_pipe<double>"
     peaks = measure_peaks(lbm, stream)     # the FP64 units at full clock before the region
     with torch.cuda.stream(stream):
         lbm.lbm_step(ctx, W)
@@ -731,11 +735,11 @@ def run_ours(args):
         "data": "synthetic",
         "config": config_json(w),
         "path": {"precision": "fp64", "audit_every": args.audit_every, "step_blocks": blocks,
-                 "kernel": "k_step<double> (32 x 2 node tiles)",
+                 "kernel": "%s (32 x 2 node tiles, %d blocks)" % (kname, blocks),
                  "timing": "CUDA events around the K steps on the launching stream"},
         "roofline": {"bound": "alu", "achieved": tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": tflops / peak_tflops, "traffic": traffic_record("k_step<double>"),
-                     "kernel": "k_step<double>",
+                     "frac": tflops / peak_tflops, "traffic": traffic_record(kname),
+                     "kernel": kname,
                      "peak_source": "measured in this run: 2 x FP64 FMA rate (lbm_probe_fma_rate)",
                      "flops_per_cell_update": FLOPS_PER_CELL,
                      "hbm_frac": BYTES_PER_CELL["fp64"] * cells / (ms * 1e-3) / 1e9 / hbm_peak,

@@ -58,6 +58,10 @@ enum lbm_precision {
                         3xTF32 tensor-core products (tcgen05, FP32
                         accumulation) over 32 x 8 node tiles; equilibria,
                         Lax-Wendroff update, moments and audits as LBM_FP32.
+                        Rows y and y + 4 of a tile share an MMA row: a
+                        non-finite population of one makes the other's
+                        update non-finite in the same step (the watchdog
+                        reports that step either way).
                         Grids with 16 x pitch x ny >= 2^32 elements are
                         LBM_ERR_UNSUPPORTED. */
   LBM_DF64 = 4,      /* double-word: each population stored as the

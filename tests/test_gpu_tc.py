@@ -76,3 +76,45 @@ def test_tc_audit_conserves_on_periodic_grid():
         assert rc == 0 and bad == -1
     finally:
         lbm.lbm_destroy(ctx)
+
+
+def _planted_nan_run(precision, node):
+    """One step from a state with one non-finite population: the first bad
+    step and the nodes whose output is not finite."""
+    from paper_0908_3749_gb300 import lbm
+    w = W.random_state(64, 16, seed=21, smooth=True)
+    cfg = lbm.make_config(w.nx, w.ny, w.dx, w.dy, w.dt, w.s, w.bc, precision, 0)
+    ctx = lbm.lbm_create(cfg)
+    try:
+        lbm.lbm_set_init(ctx, *[np.ascontiguousarray(a) for a in w.fields()])
+        lbm.lbm_step(ctx, 5)
+        f = np.empty((16, w.ny, w.nx), dtype=np.float32)
+        step = lbm.lbm_get_populations(ctx, f)
+        f[8, node[1], node[0]] = np.nan   # a diagonal population: x and y neighbours
+        lbm.lbm_set_populations(ctx, f, step)
+        lbm.lbm_step(ctx, 1)
+        rc, bad, _ = lbm.lbm_status(ctx)
+        out = np.empty_like(f)
+        lbm.lbm_get_populations(ctx, out)
+    finally:
+        lbm.lbm_destroy(ctx)
+    return step, rc, bad, set(zip(*np.nonzero(~np.isfinite(out).all(axis=0))))
+
+
+def test_tc_planted_nan_reaches_the_partner_node_and_the_watchdog():
+    """The two nodes of a thread (rows y and y + 4 of a 32 x 8 tile) share an
+    MMA row: a non-finite population of one makes the other's update
+    non-finite in the same step (zero coefficients times NaN). The watchdog
+    reports the step that holds the NaN, as the FP32 step does; the
+    non-finite outputs are the NaN node, its four stencil neighbours and, in
+    the tensor-core form only, the partner node."""
+    from paper_0908_3749_gb300 import lbm
+    node = (10, 2)                       # (x, y): tile row 2, partner row 6
+    s32, rc32, bad32, nf32 = _planted_nan_run("fp32", node)
+    stc, rctc, badtc, nftc = _planted_nan_run("tc_tf32x3", node)
+    assert rc32 == rctc == lbm.LBM_ERR_NONFINITE
+    assert bad32 == badtc == s32 == stc, (bad32, badtc, s32)
+    x, y = node
+    stencil = {(y, x), (y, x - 1), (y, x + 1), (y - 1, x), (y + 1, x)}
+    assert nf32 == stencil, nf32
+    assert nftc == stencil | {(y + 4, x)}, nftc
