@@ -45,11 +45,13 @@ def _fields(rng, H, W):
     return np.stack([rho, u, v, T])
 
 
-@pytest.mark.parametrize("loss_kind,H,W", [("mse", 13, 11), ("l1", 13, 11), ("mse", 257, 203)])
+@pytest.mark.parametrize("loss_kind,H,W", [("mse", 7, 5), ("mse", 13, 11), ("l1", 13, 11),
+                                            ("mse", 257, 203)])
 def test_gradients_match_cpu_reference(loss_kind, H, W):
-    """13 x 11: three 64-pixel chunks of the tensor-core weight gradients, the
-    last one ragged; 257 x 203: 816 chunks, so that some CTAs of the
-    persistent grid (4 per SM) accumulate two chunks in tensor memory."""
+    """7 x 5: one partial 64-pixel chunk of the tensor-core weight gradients;
+    13 x 11: three chunks, the last one ragged; 257 x 203: 816 chunks, so
+    that some CTAs of the persistent grid (4 per SM) accumulate two chunks in
+    tensor memory."""
     import torch
     from paper_0908_3749_gb300 import lbm, corrector
     rng = np.random.default_rng(0)
