@@ -90,6 +90,19 @@ def test_vn_rejects_bad_arguments_on_host(change):
     assert lbm.load().lbm_vn_last_error()
 
 
+def test_probe_rejects_bad_arguments_on_host():
+    """lbm_probe_fma_rate checks kind, output pointer and duration before it
+    touches the device."""
+    import ctypes
+    from paper_0908_3749_gb300 import lbm
+    lib = lbm.load()
+    out = ctypes.c_double()
+    for kind, millis, ptr in ((7, 50.0, ctypes.byref(out)), (-1, 50.0, ctypes.byref(out)),
+                              (0, 0.5, ctypes.byref(out)), (1, 5000.0, ctypes.byref(out)),
+                              (2, float("nan"), ctypes.byref(out)), (0, 50.0, None)):
+        assert lib.lbm_probe_fma_rate(kind, millis, ptr, None) == lbm.LBM_ERR_INVALID
+
+
 def test_eig16_rejects_empty_input():
     from paper_0908_3749_gb300 import lbm
     with pytest.raises(lbm.LBMError) as ei:

@@ -214,3 +214,19 @@ def test_c_program_on_the_abi(tmp_path):
     exe, env = _build_c_example(tmp_path)
     res = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=120)
     assert res.returncode == 0 and "abi example ok" in res.stdout, (res.returncode, res.stderr)
+
+
+def test_fma_probe_rates_are_physical_and_repeatable():
+    """The roofline denominators: every rate is positive and below the most
+    any device could retire (its multiprocessors x 128 FP32 lanes x 2.5 GHz;
+    64 FP64 lanes), the paired FP32 form retires the FP32 lane rate (the same
+    FP32 units), and a second measurement agrees within 10 %."""
+    import torch
+    from paper_0908_3749_gb300 import lbm
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    r = {k: lbm.lbm_probe_fma_rate(k, 20.0) for k in ("fp64", "fp32", "fp32x2")}
+    assert 0 < r["fp64"] <= sms * 64 * 2.5e9, r
+    assert 0 < r["fp32"] <= sms * 128 * 2.5e9, r
+    assert abs(r["fp32x2"] / r["fp32"] - 1) < 0.15, r
+    again = lbm.lbm_probe_fma_rate("fp64", 20.0)
+    assert abs(again / r["fp64"] - 1) < 0.1, (again, r)
