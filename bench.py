@@ -70,6 +70,12 @@ BYTES_PER_CELL = {"fp64": 256, "fp32": 128}
 # transform 28, conserved moments 24, equilibria 40, deviations 77,
 # back-map 64, inverse transform 28, Lax-Wendroff update 128.
 FLOPS_PER_CELL = 389
+# FP64-pipe instructions per node update of k_step<double>, counted by ncu
+# (sm__inst_executed_pipe_fp64, profiles/k_step_f64_bubble_2048x1024.md):
+# the FP64 units retire one instruction per lane slot whether it is an add,
+# a multiply or a fused multiply-add, so this count over the measured FMA
+# rate is the step's time on those units.
+FP64_INSTR_PER_CELL = 265
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -742,6 +748,8 @@ def run_ours(args):
                      "kernel": kname,
                      "peak_source": "measured in this run: 2 x FP64 FMA rate (lbm_probe_fma_rate)",
                      "flops_per_cell_update": FLOPS_PER_CELL,
+                     "fp64_pipe_frac": FP64_INSTR_PER_CELL * cells / (ms * 1e-3) / peaks["fp64_fma_per_s"],
+                     "fp64_instructions_per_cell_update": FP64_INSTR_PER_CELL,
                      "hbm_frac": BYTES_PER_CELL["fp64"] * cells / (ms * 1e-3) / 1e9 / hbm_peak,
                      "hbm_peak_gbs": hbm_peak,
                      "bytes_per_cell_update": BYTES_PER_CELL["fp64"]},
