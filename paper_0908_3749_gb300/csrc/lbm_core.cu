@@ -213,6 +213,9 @@ struct lbm_ctx {
   void* geq = nullptr;
   DevStatus* st = nullptr;
   double* partial = nullptr;
+  double* gpartial = nullptr;     // audit group sums (audit_block_done)
+  unsigned* gcount = nullptr;     // audit group counters
+  int ngroups = 0;
   double* staging = nullptr;
   void* pstage = nullptr;  // contiguous populations for host transfers (on first use)
   int nblocks = 0;      // blocks of one step launch
@@ -288,6 +291,9 @@ StepArgs<R> make_args(lbm_ctx* c, int slot) {
   A.geq3 = c->dwp ? (const float*)((const dw*)c->geq + 64) : nullptr;
   A.st = c->st;
   A.partial = c->partial;
+  A.gpartial = c->gpartial;
+  A.gcount = c->gcount;
+  A.ngroups = c->ngroups;
   A.audit_every = c->cfg.audit_every;
   A.nblocks = c->nblocks;
   A.ntiles = c->ntiles;
@@ -456,6 +462,7 @@ int reset_status(lbm_ctx* c, unsigned long long step) {
       c->cfg.audit_every > 0 ? (int)(step % (unsigned long long)c->cfg.audit_every) : 0;
   k_reset_status<<<1, 64, 0, c->stream>>>(c->st, c->cur, step, phase);
   CK(c, cudaGetLastError());
+  CK(c, cudaMemsetAsync(c->gcount, 0, sizeof(unsigned) * c->ngroups, c->stream));
   return LBM_OK;
 }
 
@@ -590,6 +597,10 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->geq, 64 * c->esize + (c->dwp ? 64 * sizeof(float) : 0));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->st, sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->partial, sizeof(double) * 4 * npartial);
+  c->ngroups = audit_groups(c->ntiles);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->gpartial, sizeof(double) * 4 * c->ngroups);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->gcount, sizeof(unsigned) * c->ngroups);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->gcount, 0, sizeof(unsigned) * c->ngroups, c->stream);
   if (e == cudaSuccess)
     e = cudaMalloc((void**)&c->staging, sizeof(double) * 4 * (size_t)C.nx * C.ny);
   if (e == cudaSuccess && c->tc) {
@@ -772,6 +783,8 @@ int lbm_destroy(lbm_ctx* c) {
   if (c->geq) cudaFree(c->geq);
   if (c->st) cudaFree(c->st);
   if (c->partial) cudaFree(c->partial);
+  if (c->gpartial) cudaFree(c->gpartial);
+  if (c->gcount) cudaFree(c->gcount);
   if (c->staging) cudaFree(c->staging);
   if (c->pstage) cudaFree(c->pstage);
   if (c->tc_b) cudaFree(c->tc_b);

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(NT, 4)
   float* const S1 = S0 + 16 * PS0;
   __shared__ double sm[NT / 4][4];
   __shared__ unsigned long long bar, s_step;
-  __shared__ int s_audit0, s_audit1, s_last;
+  __shared__ int s_audit0, s_audit1, s_alist[32], s_an;
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * FX + tx;
   const int tile = blockIdx.x;
   const int x0 = (tile % A.tiles_x) * FX, y0 = (tile / A.tiles_x) * FY;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(NT, 4)
     if (t == 0) {
       atomicExch(&A.st->tma_timeout, 1);
       mbar_wait_bounded(&bar, 0, TMA_WAIT_CYCLES);
-      audit_ticket_on_exit(A, audit0 || audit1);
+      audit_ticket_on_exit(A, audit0 || audit1, tile, A.ntiles);
     }
     return;
   }
@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(NT, 4)
     watchdog_flags(A.st, step + 1, bad, negT);
     if (audit1) audit_pair(A, tile, nb, nbb, sm);
   }
-  if (audit0 || audit1) audit_finish<NT>(A, audit0 ? step : step + 1, sm, &s_last);
+  if (audit0 || audit1)
+    audit_block_done(A, tile, A.ntiles, audit0 ? step : step + 1, s_alist, &s_an);
 }
 
 }  // namespace

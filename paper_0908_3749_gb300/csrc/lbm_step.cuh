@@ -98,12 +98,19 @@ struct StepArgs {
   const float* geq3;  // LBM_DF64: their third words; else unused
   DevStatus* st;
   double* partial;    // [ntiles][4] audit scratch: one partial sum per tile
+  double* gpartial;   // [ngroups][4]: the sums of groups of AUDIT_GROUP tiles
+  unsigned* gcount;   // [ngroups]: tiles of the group done in this audit step
+  int ngroups;
   int audit_every;
   int nblocks;        // blocks of the launch
   int ntiles, tiles_x; // node tiles of the grid (x fastest)
   double area;        // dx * dy
   int slot;           // index of the buffer read by this step (0 or 1)
 };
+
+// Tiles per group of the two-level audit sums (audit_block_done).
+constexpr int AUDIT_GROUP = 256;
+inline int audit_groups(int ntiles) { return (ntiles + AUDIT_GROUP - 1) / AUDIT_GROUP; }
 
 // FP32 -> FP64 conversion that stays inside the branch that needs it. A plain
 // conversion may be hoisted above an audit-step test by the compiler, and
@@ -378,11 +385,22 @@ __device__ __forceinline__ unsigned long long read_step(const StepArgs<R>& A, in
   return step;
 }
 
-// A block that leaves a step early (a wait timed out) still takes its audit
-// ticket so that later audit steps count their blocks correctly.
+// A block that leaves an audit step early (a wait timed out) still counts
+// its tiles (`first`, first + stride, ...; one thread), so that the group and
+// step counters return to zero for later audit steps (the failed step's
+// totals are not valid; the step reports the timeout).
 template <typename R>
-__device__ __forceinline__ void audit_ticket_on_exit(const StepArgs<R>& A, bool audit) {
-  if (audit && atomicAdd(&A.st->arrive_step, 1u) == (unsigned)A.nblocks - 1) A.st->arrive_step = 0u;
+__device__ __forceinline__ void audit_ticket_on_exit(const StepArgs<R>& A, bool audit, int first,
+                                                     int stride) {
+  if (!audit) return;
+  for (int tile = first; tile < A.ntiles; tile += stride) {
+    const int g = tile / AUDIT_GROUP, g0 = g * AUDIT_GROUP;
+    const int gn = min(A.ntiles - g0, AUDIT_GROUP);
+    if (atomicAdd(&A.gcount[g], 1u) == (unsigned)gn - 1) {
+      A.gcount[g] = 0u;
+      if (atomicAdd(&A.st->arrive_step, 1u) == (unsigned)A.ngroups - 1) A.st->arrive_step = 0u;
+    }
+  }
 }
 
 // Watchdog: records the step as the first with a bad / T <= 0 node (one
@@ -409,29 +427,100 @@ __device__ __forceinline__ void audit_tile(const StepArgs<R>& A, int tile, const
   if (t < 4) A.partial[4 * tile + t] = bs;
 }
 
-// Audit steps, once per block after its last tile: the last block to arrive
-// sums the A.ntiles partials in a fixed order into the audit ring.
-template <int N, typename R>
-__device__ __forceinline__ void audit_finish(const StepArgs<R>& A, unsigned long long step,
-                                             double (*sm)[4], int* s_last) {
-  const int t = threadIdx.y * blockDim.x + threadIdx.x;
-  __syncthreads();
-  if (t == 0) {
-    __threadfence();
-    *s_last = atomicAdd(&A.st->arrive_step, 1u) == (unsigned)A.nblocks - 1;
-  }
-  __syncthreads();
-  if (*s_last) {
-    __threadfence();
-    const double tot4 = final_sum4<N>(A.partial, A.ntiles, sm);
-    const unsigned slot = (unsigned)(A.st->audit_count & (LBM_AUDIT_RING - 1));
-    if (t < 4) A.st->audit_totals[slot][t] = tot4 * A.area;
-    __syncthreads();
-    if (t == 0) {
-      A.st->audit_steps[slot] = (long long)step;
-      A.st->audit_count += 1;
-      A.st->arrive_step = 0u;
+// Sum over a warp (fixed butterfly: every lane ends with the same value).
+__device__ __forceinline__ double warp_total(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The (rho, j_x, j_y, e) sums of rows first .. first + n - 1 of p[][4] by one
+// warp in a fixed order (lane l takes rows l, l + 32, ..., then the
+// butterfly), whichever warp of whichever block runs it; n <= AUDIT_GROUP.
+__device__ __forceinline__ void warp_sum_rows(const double* p, int first, int n, int lane,
+                                              double (&out)[4]) {
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 8
+  for (int j = lane; j < n; j += 32)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] += __ldcg(p + 4 * (first + j) + q);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out[q] = warp_total(s[q]);
+}
+
+// Audit steps, once per block after its last tile (every thread calls it;
+// the block's tiles are first, first + stride, ...): two levels of
+// fixed-order sums, so that no warp sums more than AUDIT_GROUP partials.
+// The tiles are grouped by index (group g = tiles g AUDIT_GROUP .. (g + 1)
+// AUDIT_GROUP - 1). Warp 0 counts the block's tiles into their groups'
+// counters (one lane per tile, the atomics in flight together); the groups
+// this block completes are summed in order into gpartial[], one warp per
+// group; the warp that completes the last group sums the group sums in order
+// into the audit ring. The totals do not depend on which block handled which
+// tile, and no block sums every tile's partial (which took hundreds of
+// microseconds on a 2048 x 1024 grid). Counters are reset by the warp that
+// completes them. `s_list` (32 ints) and `s_n` are shared scratch.
+template <typename R>
+__device__ __forceinline__ void audit_block_done(const StepArgs<R>& A, int first, int stride,
+                                                 unsigned long long step, int* s_list, int* s_n) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int nwarps = (int)(blockDim.x * blockDim.y) >> 5;
+  __syncthreads();  // the partials of the block's tiles are written
+  if (warp == 0) __threadfence();
+  for (int base = first; base < A.ntiles; base += 32 * stride) {
+    if (warp == 0) {
+      const int tile = base + lane * stride;
+      int g = -1;
+      if (tile < A.ntiles) {
+        const int gt = tile / AUDIT_GROUP, gn = min(A.ntiles - gt * AUDIT_GROUP, AUDIT_GROUP);
+        if (atomicAdd(&A.gcount[gt], 1u) == (unsigned)gn - 1) g = gt;
+      }
+      const unsigned done = __ballot_sync(0xffffffffu, g >= 0);
+      if (g >= 0) s_list[__popc(done & ((1u << lane) - 1u))] = g;
+      if (lane == 0) *s_n = __popc(done);
     }
+    __syncthreads();
+    const int n = *s_n;
+    if (n > 0) {
+      __threadfence();  // the groups' partials, released by the blocks that wrote them
+      for (int k = warp; k < n; k += nwarps) {
+        const int gg = s_list[k];
+        const int g0 = gg * AUDIT_GROUP, gn = min(A.ntiles - g0, AUDIT_GROUP);
+        double s4[4];
+        warp_sum_rows(A.partial, g0, gn, lane, s4);
+        if (lane < 4)
+          A.gpartial[4 * gg + lane] = lane == 0 ? s4[0] : lane == 1 ? s4[1] : lane == 2 ? s4[2] : s4[3];
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+          A.gcount[gg] = 0u;
+          __threadfence();
+          last = atomicAdd(&A.st->arrive_step, 1u) == (unsigned)A.ngroups - 1;
+        }
+        if (__shfl_sync(0xffffffffu, last, 0)) {
+          __syncwarp();
+          __threadfence();
+          double tot[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int c = 0; c < A.ngroups; c += AUDIT_GROUP) {  // chunks of groups, in order
+            double part[4];
+            warp_sum_rows(A.gpartial, c, min(A.ngroups - c, AUDIT_GROUP), lane, part);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tot[q] += part[q];
+          }
+          const unsigned slot = (unsigned)(A.st->audit_count & (LBM_AUDIT_RING - 1));
+          if (lane < 4)
+            A.st->audit_totals[slot][lane] =
+                (lane == 0 ? tot[0] : lane == 1 ? tot[1] : lane == 2 ? tot[2] : tot[3]) * A.area;
+          __syncwarp();
+          if (lane == 0) {
+            A.st->audit_steps[slot] = (long long)step;
+            A.st->audit_count += 1;
+            A.st->arrive_step = 0u;
+          }
+        }
+      }
+    }
+    __syncthreads();  // s_list and s_n are reused in the next round
   }
 }
 

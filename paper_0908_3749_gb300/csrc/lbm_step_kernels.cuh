@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, (step_minb<R, Off>
   __shared__ double sm[N / 4][4];
   __shared__ unsigned long long bar;
   __shared__ unsigned long long s_step;
-  __shared__ int s_audit, s_last;
+  __shared__ int s_audit, s_alist[32], s_an;
   const int t = threadIdx.y * Shape<R>::X + threadIdx.x;
   if (t == 0) {
     // Start the tile copy first so that its latency overlaps the read of
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, (step_minb<R, Off>
     if (t == 0) {
       atomicExch(&A.st->tma_timeout, 1);
       mbar_wait_bounded(&bar, 0, TMA_WAIT_CYCLES);
-      audit_ticket_on_exit(A, audit);
+      audit_ticket_on_exit(A, audit, (int)blockIdx.x, A.ntiles);
     }
     return;
   }
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, (step_minb<R, Off>
   step_any<R, Off, VAR>(A, fin, fout, tile, blockIdx.x, audit, A.dtr * R(s_step), sm, bad, negT);
   const unsigned long long step = s_step;
   watchdog_flags(A.st, step, bad, negT);
-  if (audit) audit_finish<N>(A, step, sm, &s_last);
+  if (audit) audit_block_done(A, (int)blockIdx.x, A.ntiles, step, s_alist, &s_an);
 }
 
 // Two tile stages (each a multiple of 128 bytes) plus room to align the first
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB_PIP
   __shared__ double sm[N / 4][4];
   __shared__ unsigned long long bar[2];
   __shared__ unsigned long long s_step;
-  __shared__ int s_audit, s_last;
+  __shared__ int s_audit, s_alist[32], s_an;
   const int t = threadIdx.y * Shape<R>::X + threadIdx.x;
   const int G = (int)gridDim.x;
   if (t == 0) {
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB_PIP
         atomicExch(&A.st->tma_timeout, 1);
         mbar_wait_bounded(&bar[s], (k >> 1) & 1, TMA_WAIT_CYCLES);
         if (more) mbar_wait_bounded(&bar[1 - s], ((k + 1) >> 1) & 1, TMA_WAIT_CYCLES);
-        audit_ticket_on_exit(A, s_audit != 0);
+        audit_ticket_on_exit(A, s_audit != 0, (int)blockIdx.x, G);
       }
       return;
     }
@@ -308,9 +308,8 @@ __global__ void __launch_bounds__(Shape<R>::X * Shape<R>::TY, Shape<R>::MINB_PIP
                      A.dtr * R(s_step), sm, bad, negT);
     __syncthreads();  // stage s and sm are free again
   }
-  const unsigned long long step = s_step;
-  watchdog_flags(A.st, step, bad, negT);
-  if (s_audit) audit_finish<N>(A, step, sm, &s_last);
+  watchdog_flags(A.st, s_step, bad, negT);
+  if (s_audit) audit_block_done(A, (int)blockIdx.x, G, s_step, s_alist, &s_an);
 }
 
 }  // namespace lbmk

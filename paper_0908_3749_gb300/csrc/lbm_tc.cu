@@ -67,8 +67,6 @@ constexpr int TC_STAGES = LBM_TC_STAGES;
 static_assert(TC_STAGES == 1 || TC_STAGES == 2, "one or two stages");
 constexpr unsigned TM_HI = 0, TM_LO = 32, TM_D = 64;  // column bases (see above)
 static_assert(TC_T == 128, "one MMA row per thread");
-static_assert(TC_T / 4 * 4 * sizeof(double) <= TC_TILE * sizeof(float),
-              "the final audit sum's scratch fits one stage");
 
 // Byte offset of element (row, k) of a rows x 32 TF32 operand in the
 // canonical K-major, no-swizzle layout: core matrices of 8 rows x 4 elements
@@ -139,7 +137,7 @@ struct TcSmem {
   unsigned tmem_base;
   double red[TC_Y][4];                         // audit sums of a tile's rows
   unsigned long long step;
-  int audit, last;
+  int audit, alist[32], an;       // audit: groups completed by this CTA
 };
 static_assert(TC_TILE * sizeof(float) % 128 == 0, "stages stay 128-byte aligned");
 
@@ -331,7 +329,7 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
       if (wait_tma >= 0) mbar_wait_bounded(&S.bar_tma[wait_tma >> 1], wait_tma & 1, TMA_WAIT_CYCLES);
       if (wait_next >= 0) mbar_wait_bounded(&S.bar_tma[wait_next >> 1], wait_next & 1, TMA_WAIT_CYCLES);
       if (wait_mma) mbar_wait_bounded(&S.bar_mma, mma_done & 1, TMA_WAIT_CYCLES);
-      audit_ticket_on_exit(A, audit);
+      audit_ticket_on_exit(A, audit, (int)blockIdx.x, G);
     }
     tc05::fence_before();
     __syncthreads();
@@ -345,9 +343,7 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
   if (warp == 0) tc05::dealloc(tmem, TC_TMEM_COLS);
 
   watchdog_flags(A.st, step, bad, negT);
-  // the final sum's scratch (N / 4 rows) in stage 0, free now: no copy is
-  // in flight and every thread has passed its last tile
-  if (audit) audit_finish<TC_T>(A, step, reinterpret_cast<double(*)[4]>(S.tile[0]), &S.last);
+  if (audit) audit_block_done(A, (int)blockIdx.x, G, step, S.alist, &S.an);
 }
 
 }  // namespace
