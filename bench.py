@@ -402,6 +402,13 @@ def large_grid_measure(torch, lbm, stream, audit_every, hbm_peak):
                 blocks = lbm.lbm_step_blocks(ctx2)
             finally:
                 lbm.lbm_destroy(ctx2)
+            ms_na = None
+            if audit_every > 0 and prec in ("fp32", "tc_tf32x3") and not fused:
+                ctx3 = make_ctx(lbm, wl, prec, 0, stream, tune=not fused)   # the same step, no audits
+                try:
+                    ms_na = time_graph_steps(torch, lbm, ctx3, stream, 64, 10)
+                finally:
+                    lbm.lbm_destroy(ctx3)
         finally:
             lbm.lbm_destroy(ctx)
         gbs = BYTES_PER_CELL["fp64" if prec == "df64" else "fp32"] * cl / (ms * 1e-3) / 1e9
@@ -409,7 +416,12 @@ def large_grid_measure(torch, lbm, stream, audit_every, hbm_peak):
                     "unit": UNIT, "ms_per_step": ms, "achieved_gbs": gbs,
                     "frac_of_hbm": gbs / hbm_peak, "step_blocks": blocks,
                     "timing": "64-step CUDA-graph replays back to back (inputs larger than L2)",
-                    "error_vs_fp64_gpu_after_%d_steps" % nsteps: err, "status": list(st)}
+                    "error_vs_fp64_gpu_after_%d_steps" % nsteps: err, "status": list(st),
+                    "audit_every": audit_every}
+        if ms_na is not None:
+            out[key]["ms_per_step_no_audit"] = ms_na
+            out[key]["frac_of_hbm_no_audit"] = (BYTES_PER_CELL["fp32"] * cl / (ms_na * 1e-3) / 1e9
+                                                / hbm_peak)
         if prec == "fp32_dwmom":
             out[key]["note"] = ("FP32 step with the conserved moments, Eq. 14 equilibria and "
                                 "temperature in double-word arithmetic (LBM_FP32_DWMOM)")
