@@ -472,17 +472,20 @@ __device__ __forceinline__ void step_tile_dw(const StepArgs<dw>& A, const dw* __
       }
     }
   }
-  if (audit) {  // FP64 only on audit steps
-    double v[NL][4];
+  if (audit) {  // double-word warp sums, FP64 across warps, only on audit steps
+    float h[NL][4], l[NL][4];
 #pragma unroll
     for (int k = 0; k < NL; ++k)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[k][q] = widen(mc[k][q]);
+      for (int q = 0; q < 4; ++q) {
+        h[k][q] = mc[k][q].h;
+        l[k][q] = mc[k][q].l;
+      }
     if constexpr (NL == 2) {
-      audit_pair_rows<BXD, BYD>(A, cur, v[0], v[1], sm);
+      audit_pair_rows<BXD, BYD>(A, cur, h[0], l[0], h[1], l[1], sm);
     } else {
       constexpr int N = BXD * BYD;
-      audit_tile<N>(A, cur, v[0], sm);
+      audit_tile_dw<N>(A, cur, h[0], l[0], sm);
     }
   }
 }

@@ -193,29 +193,14 @@ __device__ __forceinline__ unsigned long long read_step2(const StepArgs<float>& 
   return step;
 }
 
-// The tile's audit partial from the tile nodes' conserved moments, in the
-// order of the one-step kernel (warp sums of rows ya and ya + FHY, then the
-// rows 0 .. FY-1 in turn), so that fused and single steps audit bit for bit
-// alike.
+// The tile's audit partial from the tile nodes' conserved moments, by the
+// one-step kernel's reduction (audit_pair_rows), so that fused and single
+// steps audit bit for bit alike.
 __device__ __forceinline__ void audit_pair(const StepArgs<float>& A, int tile,
                                            const float (&mca)[4], const float (&mcb)[4],
                                            double (*sm)[4]) {
-  const int lane = threadIdx.x;
-  const double va[4] = {widen(mca[0]), widen(mca[1]), widen(mca[2]), widen(mca[3])};
-  const double vb[4] = {widen(mcb[0]), widen(mcb[1]), widen(mcb[2]), widen(mcb[3])};
-  const double ka = warp_sum4(va, lane), kb = warp_sum4(vb, lane);
-  if ((lane & 7) == 0) {
-    sm[threadIdx.y][lane >> 3] = ka;
-    sm[threadIdx.y + FHY][lane >> 3] = kb;
-  }
-  __syncthreads();
-  const int t = threadIdx.y * FX + threadIdx.x;
-  if (t < 4) {
-    double s = 0.0;
-    for (int w = 0; w < FY; ++w) s += sm[w][t];
-    A.partial[4 * tile + t] = s;
-  }
-  __syncthreads();
+  const float z[4] = {0.f, 0.f, 0.f, 0.f};
+  audit_pair_rows<FX, FY>(A, tile, mca, z, mcb, z, sm);
 }
 
 template <typename Off>

@@ -142,6 +142,35 @@ __device__ __forceinline__ double warp_sum4(const double v[4], int lane) {
   return k;
 }
 
+// The same for FP32 values, exactly to double-word accuracy on the FP32
+// units: each value is an unevaluated pair h + l; an addition keeps the exact
+// rounding error of the high words (TwoSum) and adds it and the low words
+// into the low word, so a warp total of FP32 values carries about 48
+// significant bits (errors of order 2^-48 of the summed magnitudes), and
+// the FP64 units, slow on GB300, see only the warp totals.
+__device__ __forceinline__ void dw_acc(float& h, float& l, float h2, float l2) {
+  float s, e;
+  two_sum(h, h2, s, e);
+  h = s;
+  l = (l + l2) + e;
+}
+__device__ __forceinline__ double warp_sum4_dw(const float (&h)[4], const float (&l)[4], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8;
+  float k0h = h16 ? h[2] : h[0], k0l = h16 ? l[2] : l[0];
+  float k1h = h16 ? h[3] : h[1], k1l = h16 ? l[3] : l[1];
+  const float s0h = h16 ? h[0] : h[2], s0l = h16 ? l[0] : l[2];
+  const float s1h = h16 ? h[1] : h[3], s1l = h16 ? l[1] : l[3];
+  dw_acc(k0h, k0l, __shfl_xor_sync(0xffffffffu, s0h, 16), __shfl_xor_sync(0xffffffffu, s0l, 16));
+  dw_acc(k1h, k1l, __shfl_xor_sync(0xffffffffu, s1h, 16), __shfl_xor_sync(0xffffffffu, s1l, 16));
+  float kh = h8 ? k1h : k0h, kl = h8 ? k1l : k0l;
+  const float sh = h8 ? k0h : k1h, sl = h8 ? k0l : k1l;
+  dw_acc(kh, kl, __shfl_xor_sync(0xffffffffu, sh, 8), __shfl_xor_sync(0xffffffffu, sl, 8));
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1)
+    dw_acc(kh, kl, __shfl_xor_sync(0xffffffffu, kh, o), __shfl_xor_sync(0xffffffffu, kl, o));
+  return widen(kh) + widen(kl);  // exact in FP64
+}
+
 // Block sum of v[0..3] (N threads); threads 0..3 return sums 0..3.
 template <int N>
 __device__ __forceinline__ double block_sum4(const double v[4], double (*sm)[4]) {
@@ -415,6 +444,23 @@ __device__ __forceinline__ void watchdog_flags(DevStatus* st, unsigned long long
   }
 }
 
+// Audit steps, per tile, for FP32 or double-word values (h + l): warp totals
+// by warp_sum4_dw, then the warps' totals in FP64 in order.
+template <int N, typename R>
+__device__ __forceinline__ void audit_tile_dw(const StepArgs<R>& A, int tile, const float (&h)[4],
+                                              const float (&l)[4], double (*sm)[4]) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const double k = warp_sum4_dw(h, l, lane);
+  if ((lane & 7) == 0) sm[warp][lane >> 3] = k;
+  __syncthreads();
+  if (t < 4) {
+    double s = 0.0;
+    for (int w = 0; w < N / 32; ++w) s += sm[w][t];
+    A.partial[4 * tile + t] = s;
+  }
+}
+
 // Audit steps, per tile: the block's FP64 sums of (rho, j_x, j_y, e) over the
 // tile go to partial[tile]. Per tile rather than per block, so the totals do
 // not depend on which block handled which tile. `v` is zero for inactive
@@ -525,22 +571,30 @@ __device__ __forceinline__ void audit_block_done(const StepArgs<R>& A, int first
 }
 
 // Audit partial of a tile whose threads each hold two nodes (rows y and
-// y + BYD/2): two warp passes, then the rows 0 .. BYD-1 in order.
+// y + BYD/2), FP32 or double-word values (h + l): the thread's two nodes
+// added exactly to double-word accuracy, the warp totals by warp_sum4_dw,
+// then the warps (rows 0 .. BYD/2 - 1) in FP64 in order.
 template <int BXD, int BYD, typename R>
-__device__ __forceinline__ void audit_pair_rows(const StepArgs<R>& A, int cur, const double (&va)[4],
-                                                const double (&vb)[4], double (*sm)[4]) {
+__device__ __forceinline__ void audit_pair_rows(const StepArgs<R>& A, int cur,
+                                                const float (&ha)[4], const float (&la)[4],
+                                                const float (&hb)[4], const float (&lb)[4],
+                                                double (*sm)[4]) {
   constexpr int HY = BYD / 2;
   const int lane = threadIdx.x;
-  const double ka = warp_sum4(va, lane), kb = warp_sum4(vb, lane);
-  if ((lane & 7) == 0) {
-    sm[threadIdx.y][lane >> 3] = ka;
-    sm[threadIdx.y + HY][lane >> 3] = kb;
+  float h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    h[q] = ha[q];
+    l[q] = la[q];
+    dw_acc(h[q], l[q], hb[q], lb[q]);
   }
+  const double k = warp_sum4_dw(h, l, lane);
+  if ((lane & 7) == 0) sm[threadIdx.y][lane >> 3] = k;
   __syncthreads();
   const int t = threadIdx.y * BXD + threadIdx.x;
   if (t < 4) {
     double s = 0.0;
-    for (int w = 0; w < BYD; ++w) s += sm[w][t];
+    for (int w = 0; w < HY; ++w) s += sm[w][t];
     A.partial[4 * cur + t] = s;
   }
 }

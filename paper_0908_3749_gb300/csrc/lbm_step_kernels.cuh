@@ -181,19 +181,22 @@ __device__ __forceinline__ void step_tile_x2(const StepArgs<float>& A, const flo
       }
     }
   }
-  if (audit) {  // FP64 only on audit steps
-    double va[4], vb[4];
+  if (audit) {  // double-word warp sums, FP64 across warps, only on audit steps
+    float ha[4], la[4], hb[4], lb[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if constexpr (MAC) {
-        va[q] = act_a ? widen(wca[q]) : 0.0;
-        vb[q] = act_b ? widen(wcb[q]) : 0.0;
+        ha[q] = act_a ? wca[q].h : 0.f;
+        la[q] = act_a ? wca[q].l : 0.f;
+        hb[q] = act_b ? wcb[q].h : 0.f;
+        lb[q] = act_b ? wcb[q].l : 0.f;
       } else {
-        va[q] = widen(mca[q]);
-        vb[q] = widen(mcb[q]);
+        ha[q] = mca[q];
+        hb[q] = mcb[q];
+        la[q] = lb[q] = 0.f;
       }
     }
-    audit_pair_rows<BXD, BYD>(A, cur, va, vb, sm);
+    audit_pair_rows<BXD, BYD>(A, cur, ha, la, hb, lb, sm);
   }
 }
 

@@ -306,13 +306,8 @@ __global__ void __launch_bounds__(TC_T, TC_CTAS_PER_SM)
       }
     }
     if (audit) {  // per-tile partial (fixed order whatever the CTA)
-      double va[4], vb[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        va[c] = widen(mca[c]);
-        vb[c] = widen(mcb[c]);
-      }
-      audit_pair_rows<TC_X, TC_Y>(A, cur, va, vb, S.red);
+      const float z[4] = {0.f, 0.f, 0.f, 0.f};
+      audit_pair_rows<TC_X, TC_Y>(A, cur, mca, z, mcb, z, S.red);
     }
     // stage s and TMEM are free for the next tile
     tc05::fence_before();
