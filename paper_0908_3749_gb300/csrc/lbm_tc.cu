@@ -7,7 +7,8 @@
 // thread t = (tx, ty) holds two of them, rows ty and ty + 4 (nodes a and b),
 // and computes both in paired f32x2 instructions, as the FP32 step does.
 // Both nodes of thread t are row t of the MMAs (lane t of tensor memory):
-// the A row holds node a's 16 values in K = 0..15 and node b's in 16..31,
+// the A row holds the two nodes' 16 values interleaved (K = 2j for value j of
+// node a, 2j + 1 for node b: the thread's register pairs, split in pairs),
 // and B (32 x 32) maps them to interleaved output columns, 2k for moment k
 // of node a and 2k + 1 for node b, so that one 32-column load gives every
 // thread its pairs ready for the paired arithmetic. (The other node's values
@@ -104,21 +105,21 @@ __device__ __forceinline__ unsigned tf32_rna_bits(float x) {
 }
 
 // The TF32 high and low parts of the two nodes' 16 values into this
-// thread's lane of the A columns: hi = tf32(v), lo = v - hi (exact; the
-// product reads its 19 high bits).
+// thread's lane of the A columns, interleaved: hi = tf32(v), lo = v - hi
+// (exact, one paired subtraction for both nodes; the product reads its 19
+// high bits).
 __device__ __forceinline__ void put_split(unsigned tmem_lane, const F2 (&v)[16]) {
+  unsigned h[32], l[32];
 #pragma unroll
-  for (int n = 0; n < 2; ++n) {
-    unsigned h[16], l[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float x = n ? v[k].v.y : v[k].v.x;
-      h[k] = tf32_rna_bits(x);
-      l[k] = __float_as_uint(__fsub_rn(x, __uint_as_float(h[k])));
-    }
-    tc05::st16(tmem_lane + TM_HI + 16 * n, h);
-    tc05::st16(tmem_lane + TM_LO + 16 * n, l);
+  for (int k = 0; k < 16; ++k) {
+    h[2 * k] = tf32_rna_bits(v[k].v.x);
+    h[2 * k + 1] = tf32_rna_bits(v[k].v.y);
+    const F2 lo = v[k] - F2(__uint_as_float(h[2 * k]), __uint_as_float(h[2 * k + 1]));
+    l[2 * k] = __float_as_uint(lo.v.x);
+    l[2 * k + 1] = __float_as_uint(lo.v.y);
   }
+  tc05::st32(tmem_lane + TM_HI, h);
+  tc05::st32(tmem_lane + TM_LO, l);
   tc05::st_wait();
 }
 
@@ -359,7 +360,7 @@ float tf32_host(float x) {  // round to nearest (ties away), 10 mantissa bits ke
 
 // Canonical-layout TF32 hi/lo parts of the 32 x 32 B operands of M and
 // M^-1, 4 x 4 KB. Row n of B^T (output column n = 2k + node) takes K index
-// node * 16 + j (population or moment j of that node): the entry of row k,
+// 2j + node (population or moment j of that node): the entry of row k,
 // column j of M (m = f M^T) or of M^-1 (df = dm M^-T); zero for the other
 // node. Relaxation weights w_k = -dt s_k are applied on the CUDA cores.
 void tc_prepare_constants(const double (&M)[16][16], const double (&Minv)[16][16],
@@ -372,7 +373,7 @@ void tc_prepare_constants(const double (&M)[16][16], const double (&Minv)[16][16
       const float ml = tf32_host((float)(M[k][j] - (double)mh));
       const float il = tf32_host((float)(Minv[k][j] - (double)ih));
       for (int node = 0; node < 2; ++node) {
-        const unsigned off = canon(2 * k + node, 16 * node + j);
+        const unsigned off = canon(2 * k + node, 2 * j + node);
         memcpy(out[0] + off, &mh, 4);
         memcpy(out[1] + off, &ml, 4);
         memcpy(out[2] + off, &ih, 4);
