@@ -216,6 +216,7 @@ struct lbm_ctx {
   double* gpartial = nullptr;     // audit group sums (audit_block_done)
   unsigned* gcount = nullptr;     // audit group counters
   int ngroups = 0;
+  int agroup = 0;                 // tiles per audit group
   double* staging = nullptr;
   void* pstage = nullptr;  // contiguous populations for host transfers (on first use)
   int nblocks = 0;      // blocks of one step launch
@@ -294,6 +295,7 @@ StepArgs<R> make_args(lbm_ctx* c, int slot) {
   A.gpartial = c->gpartial;
   A.gcount = c->gcount;
   A.ngroups = c->ngroups;
+  A.agroup = c->agroup;
   A.audit_every = c->cfg.audit_every;
   A.nblocks = c->nblocks;
   A.ntiles = c->ntiles;
@@ -597,7 +599,8 @@ int lbm_create(const lbm_config* cfg, void* cuda_stream, lbm_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->geq, 64 * c->esize + (c->dwp ? 64 * sizeof(float) : 0));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->st, sizeof(DevStatus));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->partial, sizeof(double) * 4 * npartial);
-  c->ngroups = audit_groups(c->ntiles);
+  c->agroup = (c->esize == 8 && !c->dwp) ? AUDIT_GROUP_FP64 : AUDIT_GROUP_REDUCED;
+  c->ngroups = audit_groups(c->ntiles, c->agroup);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->gpartial, sizeof(double) * 4 * c->ngroups);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->gcount, sizeof(unsigned) * c->ngroups);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->gcount, 0, sizeof(unsigned) * c->ngroups, c->stream);
